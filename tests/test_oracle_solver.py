@@ -1,0 +1,144 @@
+"""Pins of the oracle's residual, explicit step and V-cycle (Sec. 2.2, 2.4, 4.2 of the paper):
+free-stream preservation, discrete conservation, the 1-level V-cycle, determinism and design
+order on a smooth travelling density wave."""
+import numpy as np
+
+import meshgen as mg
+
+
+def _uniform(orc, mesh, **kw):
+    M = orc.Mesh(mesh)
+    S = orc.Solver(M, orc.params(**kw))
+    W, G = mg.uniform_state(M.nc, mach=kw.get("mach", 0.2), aoa=kw.get("aoa", (0.0, 0.0)))
+    S.set_state(W, G)
+    return M, S, W
+
+
+def test_free_stream_preserved_on_jittered_mixed_mesh(orc):
+    M, S, W = _uniform(orc, mg.periodic_box(6), mach=0.3, aoa=(20.0, 10.0))
+    vol, _, _ = M.cells()
+    r = S.residual()
+    flux_scale = np.abs(W).max() * vol.max() ** (2.0 / 3.0)
+    assert np.abs(r["res"]).max() < 1e-13 * flux_scale
+    assert np.abs(r["grad"]).max() < 1e-12
+    np.testing.assert_allclose(r["alpha"], 1.0, atol=1e-15)
+    S.run(2, multigrid=True)
+    Wn, Gn, _ = S.state()
+    np.testing.assert_allclose(Wn, W, rtol=0, atol=1e-13)
+
+
+def test_free_stream_preserved_with_slip_walls_and_farfield(orc):
+    """A uniform flow parallel to slip walls, with farfield (Riemann-invariant) in/outflow."""
+    mesh = mg.box_mesh(5, 4, 4, mg.quadrant_split(3, 3), periodic=(False, False, True), jitter=0.05,
+                       bc=dict(xmin=3, xmax=3, ymin=1, ymax=1))
+    M, S, W = _uniform(orc, mesh, mach=0.4)
+    vol, _, _ = M.cells()
+    r = S.residual()
+    assert np.abs(r["res"]).max() < 1e-13 * np.abs(W).max() * vol.max() ** (2.0 / 3.0)
+    S.run(2, multigrid=True)
+    Wn, _, _ = S.state()
+    np.testing.assert_allclose(Wn, W, rtol=0, atol=1e-13)
+
+
+def _wave(orc, n=6, **kw):
+    mesh = mg.periodic_box(n)
+    M = orc.Mesh(mesh)
+    S = orc.Solver(M, orc.params(mach=0.2, **kw))
+    W, G = mg.density_wave_state(mesh)
+    S.set_state(W, G)
+    return M, S, W, G
+
+
+def test_fluxes_telescope_on_periodic_mesh(orc):
+    M, S, W, _ = _wave(orc)
+    r = S.residual()
+    tot = r["res"].sum(axis=1)
+    assert np.all(np.abs(tot) < 1e-14 * np.abs(r["res"]).sum(axis=1).max())
+
+
+def test_vcycle_conserves_total_mass_momentum_energy(orc):
+    """With one global time step per level, sum |Omega| W is conserved by the fine step, and the
+    coarse corrections add sum_c dt (Res_c + F_c) = 0 because every residual telescopes."""
+    M, S, W, _ = _wave(orc, dt_mode=1)
+    vol, _, _ = M.cells()
+    before = W @ vol
+    S.run(3, multigrid=True)
+    Wn, _, _ = S.state()
+    np.testing.assert_allclose(Wn @ vol, before, rtol=1e-14, atol=1e-15)
+
+
+def test_one_level_vcycle_is_the_single_grid_step(orc):
+    _, S1, _, _ = _wave(orc, n_levels=1)
+    _, S2, _, _ = _wave(orc, n_levels=3)
+    h1 = S1.run(3, multigrid=True)
+    h2 = S2.run(3, multigrid=False)
+    assert np.array_equal(h1, h2)
+    for a, b in zip(S1.state(), S2.state()):
+        assert np.array_equal(a, b)
+
+
+def test_runs_are_bitwise_reproducible(orc):
+    _, S1, _, _ = _wave(orc)
+    _, S2, _, _ = _wave(orc)
+    assert np.array_equal(S1.run(2, multigrid=True), S2.run(2, multigrid=True))
+    for a, b in zip(S1.state(), S2.state()):
+        assert np.array_equal(a, b)
+
+
+def test_kfvs_levels_free_stream_and_telescoping(orc):
+    M, S, W = _uniform(orc, mg.periodic_box(8), mach=0.3, aoa=(10.0, 0.0))
+    for lev in (1, 2):
+        L = S.level(lev)
+        Wl = np.repeat(W[:, :1], L["nc"], axis=1)
+        R = S.kfvs_residual(lev, Wl)
+        assert np.abs(R).max() < 1e-13 * L["area"].max()
+        rng = np.random.default_rng(lev)
+        Wp = Wl * (1.0 + 0.01 * rng.normal(size=Wl.shape))
+        R = S.kfvs_residual(lev, Wp)
+        assert np.all(np.abs(R.sum(axis=1)) < 1e-14 * np.abs(R).sum(axis=1).max())
+
+
+def _wave_error(orc, n, cfl, T=0.1):
+    mesh = mg.box_mesh(n, 4, 4, lambda i, j, k: np.zeros(np.shape(i), int), periodic=(True, True, True))
+    M = orc.Mesh(mesh)
+    pts, w = M.qpoints(4)
+    vol = w.sum(1)
+    U, g = 0.2, 1.4
+
+    def avg(t):
+        ph = 2 * np.pi * (pts[..., 0] - U * t)
+        rho, drho = 1 + 0.01 * np.sin(ph), 0.02 * np.pi * np.cos(ph)
+        R, D = (w * rho).sum(1) / vol, (w * drho).sum(1) / vol
+        Wv = np.stack([R, U * R, 0 * R, 0 * R, 1 / g / (g - 1) + 0.5 * U * U * R])
+        G = np.zeros((15, M.nc))
+        G[0], G[3], G[12] = D, U * D, 0.5 * U * U * D
+        return Wv, G
+
+    def solver(c):
+        return orc.Solver(M, orc.params(mach=U, dt_mode=1, n_levels=1, cfl_fine=c))
+
+    S = solver(cfl)
+    S.set_state(*avg(0.0))
+    t = 0.0
+    while t < T - 1e-14:
+        dt = S.residual()["dt"][0]
+        if t + dt > T:
+            last = solver(cfl * (T - t) / dt)
+            last.set_state(*S.state())
+            last.run(1)
+            S, t = last, T
+            break
+        S.run(1)
+        t += dt
+    We, _ = avg(T)
+    Wn, _, _ = S.state()
+    return np.sum(vol * np.abs(Wn[0] - We[0])) / vol.sum()
+
+
+def test_design_order_on_smooth_density_wave(orc):
+    """Third-order reconstruction with second-order time accuracy: on hexahedra at CFL 0.2 the
+    error of a travelling density wave falls at a rate of at least 2.2 per grid halving."""
+    e1 = _wave_error(orc, 16, 0.2)
+    e2 = _wave_error(orc, 32, 0.2)
+    assert e1 < 2e-5
+    assert np.log2(e1 / e2) > 2.2
