@@ -1,0 +1,169 @@
+/* cgks.h - C ABI of libcgks, a GB300 (sm_103a) implementation of the multigrid compact gas-kinetic
+ * scheme (CGKS) for steady flows on 3D mixed hexahedral/prismatic/tetrahedral meshes
+ * (H. Liu, X. Ji, Y. Mao, Y. Ding, K. Xu, arXiv:2402.02075).
+ *
+ * Conventions shared by every entry point
+ *  - Every call returns a cgks_status; CGKS_OK is 0.  On any other value cgks_last_error() gives a
+ *    one-line message.  No C++ exception crosses this boundary.
+ *  - Array arguments are DEVICE pointers (memory of the current CUDA device) unless the comment says
+ *    "host".  The caller owns every pointer it passes; the library copies what it keeps.
+ *  - Field arrays are component-major: W is double[5][N] (rho, rho u, rho v, rho w, rho E), the
+ *    cell-averaged gradient gradW is double[15][N] with row 3*q + d = d(W_q)/dx_d.
+ *  - Work is enqueued on the CUDA stream given to cgks_create (stream order); calls return after
+ *    enqueueing, except those with host outputs, which synchronise that stream before returning.
+ *  - Non-dimensionalisation: free stream rho = 1, p = 1/gamma (unit sound speed), |U| = mach along
+ *    the angles aoa; viscosity mu = mach / reynolds (reference length 1), constant.
+ *  - Boundary-face tags: 1 slip wall, 2 no-slip adiabatic wall, 3 farfield (Riemann invariants),
+ *    4 supersonic inflow, 5 supersonic outflow (extrapolation), >= 100 periodic side.
+ */
+#ifndef CGKS_H
+#define CGKS_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CGKS_OK = 0,
+  CGKS_EINVAL = 1,       /* bad argument (null pointer, size, level out of range, state not set) */
+  CGKS_ENOMEM = 2,       /* device allocation failed */
+  CGKS_ECUDA = 3,        /* a CUDA call failed; the message carries cudaGetErrorString */
+  CGKS_EMESH = 4,        /* inconsistent mesh (unmatched face, bad cell type, non-positive volume) */
+  CGKS_ENAN = 5,         /* non-finite value or rho <= 0 / p <= 0 in a state; message names the cell */
+  CGKS_ENOTCONV = 6,     /* steady solve reached max_iters before the requested drop */
+  CGKS_ETIMEOUT = 7,     /* reserved for bounded device-side waits (none are used) */
+  CGKS_EUNSUPPORTED = 8  /* entry point or option not available in this build */
+} cgks_status;
+
+typedef struct cgks_ctx cgks_ctx; /* opaque, owned by the library */
+
+/* Solver parameters.  Defaults (cgks_default_params) are the paper's constants where it gives them
+ * and documented readings where it does not. */
+typedef struct {
+  double gamma;        /* ratio of specific heats, internal degrees K = (5 - 3 gamma)/(gamma - 1) (Sec. 2.1) */
+  double mach;         /* free-stream Mach number */
+  double reynolds;     /* Reynolds number (reference length 1); used when viscous != 0 */
+  double prandtl;      /* Prandtl number; the BGK model has Pr = 1, other values correct the heat flux */
+  double aoa[2];       /* degrees: angle of attack (x-z plane) and sideslip of the free stream */
+  double cfl_fine;     /* CFL number of the fine-level local time step */
+  double cfl_coarse;   /* CFL number of the coarse-level (KFVS) local time step */
+  double eps_inviscid; /* epsilon in tau_n = eps dt + C |p_l - p_r|/(p_l + p_r) dt (Sec. 2.3, 0.01) */
+  double c_press;      /* C of the pressure-jump term of tau_n (Sec. 2.3, 1) */
+  double weno_eps;     /* epsilon of the non-linear WENO weights (Sec. 3.4, 1e-5) */
+  double skew_min;     /* skewness limit of the coarsening (Sec. 4.1; no value given, 0.2) */
+  int32_t n_levels;    /* multigrid levels including the fine one (Sec. 4.2 uses 3) */
+  int32_t pre;         /* fine pre-smoothing steps per V-cycle (Sec. 4.2: 1) */
+  int32_t post;        /* post-smoothing steps per level (Sec. 4.2: 0) */
+  int32_t coarse_steps;     /* forward-Euler KFVS steps per coarse level and cycle (1) */
+  int32_t passes_per_level; /* pairwise coarsening passes per multigrid level (2) */
+  int32_t viscous;     /* 0 Euler, 1 Navier-Stokes (tau = mu/p) */
+  int32_t dt_mode;     /* 0 local time steps, 1 one global (minimum) time step per level */
+  int32_t precision;   /* 0 FP64 on every level; 1 FP32 coarse levels (not available: EUNSUPPORTED) */
+  uint64_t agglo_seed; /* 0: the paper's hash on cell ids; s > 0 relabels cell N as splitmix64(N ^ s) >> 33 */
+} cgks_params;
+
+/* Fills *p with the defaults listed above (gamma 1.4, mach 0.2, reynolds 1e4, prandtl 1, aoa 0,
+ * cfl 0.5/0.5, eps 0.01, C 1, weno 1e-5, skew 0.2, 3 levels, pre 1, post 0, 1 coarse step,
+ * 2 passes, inviscid, local time steps, FP64, seed 0).  Host pointer. */
+cgks_status cgks_default_params(cgks_params* p);
+
+/* Creates a context on the current CUDA device.  params: host pointer, copied.  stream: a
+ * cudaStream_t (NULL = legacy default stream) on which all work of this context is enqueued. */
+cgks_status cgks_create(const cgks_params* params, void* cuda_stream, cgks_ctx** out);
+
+/* Frees every device and host buffer of the context.  NULL is accepted. */
+cgks_status cgks_destroy(cgks_ctx* ctx);
+
+/* Replaces the parameters (host pointer).  Options that shape the multigrid hierarchy
+ * (n_levels, passes_per_level, skew_min, agglo_seed) take effect at the next cgks_mesh_upload. */
+cgks_status cgks_set_params(cgks_ctx* ctx, const cgks_params* params);
+
+/* Uploads the fine mesh (all HOST pointers, copied) and builds on the device: faces and their
+ * Gauss points (3 per triangle, 4 per quadrilateral, Sec. 2.2), cell volume moments, the
+ * reconstruction operators (Sec. 3) and the coarse levels by hash agglomeration (Sec. 4.1).
+ *   xyz         double[n_nodes][3]
+ *   cell_type   int8[n_cells]: 4 tetrahedron, 5 prism, 6 hexahedron; nodes in VTK order
+ *   cell_ptr    int64[n_cells + 1] offsets into cell_nodes (4, 6 or 8 nodes per cell)
+ *   cell_nodes  int32 node ids
+ *   bface_ptr   int64[n_bfaces + 1], bface_nodes int32 (3 or 4 nodes, any order), bface_tag int32
+ *   periodic_pairs int32[n_periodic][2] boundary-face ids (nullable when n_periodic == 0); the
+ *               second face of a pair is the translate of the first.
+ * Cell ids are the upload order; the hash of Sec. 4.1 uses them.  Errors: CGKS_EMESH (a cell face
+ * matched by no cell and no boundary face, a face shared by three cells, bad type, non-positive
+ * volume), CGKS_EINVAL, CGKS_ENOMEM.  Synchronises the stream.  Replaces any earlier mesh. */
+cgks_status cgks_mesh_upload(cgks_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_cells,
+                             const int8_t* cell_type, const int64_t* cell_ptr, const int32_t* cell_nodes,
+                             int64_t n_bfaces, const int64_t* bface_ptr, const int32_t* bface_nodes,
+                             const int32_t* bface_tag, const int32_t* periodic_pairs, int64_t n_periodic);
+
+/* Sizes of multigrid level `level` (0 = fine).  Host outputs, nullable. */
+cgks_status cgks_level_info(cgks_ctx* ctx, int level, int64_t* n_cells, int64_t* n_faces);
+
+/* Map from the cells of level-1 to the cells of `level` (level >= 1): int32[n_cells(level-1)],
+ * device pointer written by the library. */
+cgks_status cgks_coarse_map(cgks_ctx* ctx, int level, int32_t* fine_to_coarse);
+
+/* Geometry of a level, device outputs (each nullable): cell volumes double[n], centroids
+ * double[3][n]; faces: left/right cell int32[nf] (right = -1 on boundary faces), tag int32[nf]
+ * (-1 interior, BC tag on boundary faces, side tag of the left cell on periodic faces), area
+ * vectors double[3][nf] (outward from the left cell, summed over the agglomerated fine faces). */
+cgks_status cgks_level_geometry(cgks_ctx* ctx, int level, double* vol, double* ctr, int32_t* face_left,
+                                int32_t* face_right, int32_t* face_tag, double* area_vec);
+
+/* Fine-level central second-moment averages double[6][N] (xx, yy, zz, xy, yz, xz). Device output. */
+cgks_status cgks_fine_moments(cgks_ctx* ctx, double* m2);
+
+/* Sets the fine state: W double[5][N]; gradW double[15][N] or NULL (zero gradients); alpha (the
+ * compression factor used by the next Green-Gauss sub-stencil, Sec. 3.3) double[N] or NULL (1).
+ * Device pointers, copied.  Resets the residual-drop reference. */
+cgks_status cgks_state_init(cgks_ctx* ctx, const double* W, const double* gradW, const double* alpha);
+
+/* Copies the fine state out (device pointers, each nullable). */
+cgks_status cgks_state_get(cgks_ctx* ctx, double* W, double* gradW, double* alpha);
+
+/* One fine residual evaluation at the current state, no update.
+ *   order 3: CGKS (HWENO reconstruction + gas-kinetic flux, Sec. 2-3); order 1: first-order KFVS.
+ *   res      double[5][N] = -(sum of outward face fluxes) of every cell (device, nullable)
+ *   gradW_new double[15][N] the Gauss-Green gradients at t + dt times the compression factor
+ *            (Sec. 2.4, 3.3; order 3 only; device, nullable)
+ *   alpha_new double[N] the compression factor (order 3 only; device, nullable)
+ *   dt       double[N] local time steps used by the faces (device, nullable)
+ *   norm     host double: sqrt(mean over cells of (res_rho / |Omega|)^2) (nullable; synchronises) */
+cgks_status cgks_residual(cgks_ctx* ctx, int order, double* res, double* gradW_new, double* alpha_new,
+                          double* dt, double* norm);
+
+/* First-order KFVS residual of level `level` for the state W double[5][n_level] (device in/out). */
+cgks_status cgks_kfvs_residual(cgks_ctx* ctx, int level, const double* W, double* res);
+
+/* n_steps explicit single-grid CGKS steps (Eq. smo).  norm_hist: host double[n_steps] of the
+ * residual norm before each step (nullable; synchronises).  CGKS_ENAN if a state becomes
+ * non-physical (checked at the end of the call). */
+cgks_status cgks_step(cgks_ctx* ctx, int n_steps, double* norm_hist);
+
+/* n_cycles V-cycles (Sec. 4.2): pre-smoothing CGKS step(s), defect at the new state, FAS coarse
+ * levels with KFVS forward-Euler smoothing, injection correction.  norm_hist as in cgks_step. */
+cgks_status cgks_vcycle(cgks_ctx* ctx, int n_cycles, double* norm_hist);
+
+/* Iterates cgks_vcycle (multigrid != 0) or cgks_step until the residual norm falls below
+ * drop x (first norm) or max_iters iterations.  Host outputs (nullable): iterations done, final
+ * norm ratio, wall seconds.  The norm is read every `check_every` = 10 iterations.
+ * CGKS_ENOTCONV when max_iters is reached first. */
+cgks_status cgks_steady_solve(cgks_ctx* ctx, int multigrid, double drop, int64_t max_iters, int64_t* iters_done,
+                              double* final_drop, double* seconds);
+
+/* Discrete adjoint of the residual (extension, not in the paper).  Returns CGKS_EUNSUPPORTED. */
+cgks_status cgks_adjoint(cgks_ctx* ctx, const double* wall_disp_modes, int n_modes, double* dJ_dmodes,
+                         double* dJ_dmach);
+
+/* Measured FP64 fused-multiply-add throughput of the current device in TFLOP/s (host output),
+ * from a register-resident FMA chain kernel; the roofline denominator of the FP64-bound kernels. */
+cgks_status cgks_fp64_peak(double* tflops);
+
+/* Text of the last error of ctx (or of the last failed cgks_create when ctx is NULL). */
+const char* cgks_last_error(const cgks_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

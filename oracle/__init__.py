@@ -103,6 +103,7 @@ def lib():
         _lib.orc_pt_frame.argtypes = [d, d, d]
         _lib.orc_pt_hash.restype = C.c_uint64
         _lib.orc_pt_hash.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64]
+        _lib.orc_term_scales.argtypes = [P, d, d]
         _lib.orc_pt_splitmix64.restype = C.c_uint64
         _lib.orc_pt_splitmix64.argtypes = [C.c_uint64]
     return _lib
@@ -205,7 +206,11 @@ class Solver:
                                 _p(dt, C.c_double), _p(nm, C.c_double))
         if rc:
             raise RuntimeError(f"oracle residual failed ({rc})")
-        return dict(res=R, grad=G, alpha=a, dt=dt, norm=float(nm[0]))
+        fs, gs = np.zeros((5, n)), np.zeros((5, n))
+        lib().orc_term_scales(self.h, _p(fs, C.c_double), _p(gs, C.c_double))
+        # fscale: per cell and component, sum over its Gauss points of |weight x flux| (the terms the
+        # residual adds up); gscale: the same for |weight x interface state| / |Omega| (gradients)
+        return dict(res=R, grad=G, alpha=a, dt=dt, norm=float(nm[0]), fscale=fs, gscale=gs)
 
     def run(self, n, multigrid=False):
         h = np.zeros(max(n, 1))

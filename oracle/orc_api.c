@@ -277,3 +277,8 @@ int orc_pt_ghost(const orc_params* P, int tag, const double* n, const double* W,
 void orc_pt_frame(const double* n, double* t1, double* t2) { orc_frame(n, t1, t2); }
 uint64_t orc_pt_hash(uint64_t nl, uint64_t nr, uint64_t nf) { return orc_face_hash(nl, nr, nf); }
 uint64_t orc_pt_splitmix64(uint64_t x) { return orc_splitmix64(x); }
+
+int orc_solver_term_scales(orc_solver* S, double* fabs_out, double* gabs_out);
+int orc_term_scales(void* hp, double* fabs_out, double* gabs_out) {
+  return orc_solver_term_scales(((handle*)hp)->S, fabs_out, gabs_out);
+}

@@ -350,6 +350,13 @@ static void local_dt_level(const orc_solver* S, const orc_level* L, const double
 /* ------------------------------------------------------------------------------------------- */
 /* residuals                                                                                    */
 
+/* magnitudes of the terms the last fine residual summed: per cell and component, the sum over its
+   Gauss points of |weight x flux| and of |weight x interface state| / |Omega| (the scales of the
+   residual and of the Gauss-Green gradient sums; used by tests as rounding-error denominators) */
+static double* g_last_fabs = NULL;
+static double* g_last_gabs = NULL;
+static int64_t g_last_n = 0;
+
 /* fine CGKS residual: Res [nc][5], new gradients (already scaled by the compression factor) and
    the compression factor; any output may be NULL */
 int orc_residual_fine(orc_solver* S, const double* W, const double* G, const double* alpha_prev, double* Res,
@@ -408,6 +415,15 @@ int orc_residual_fine(orc_solver* S, const double* W, const double* G, const dou
     rc_ = -1;
     goto out;
   }
+  if (g_last_n != nc) {
+    free(g_last_fabs);
+    free(g_last_gabs);
+    g_last_fabs = malloc(sizeof(double) * 5 * nc);
+    g_last_gabs = malloc(sizeof(double) * 5 * nc);
+    g_last_n = nc;
+  }
+  memset(g_last_fabs, 0, sizeof(double) * 5 * nc);
+  memset(g_last_gabs, 0, sizeof(double) * 5 * nc);
   for (int64_t f = 0; f < M->nf; ++f) {
     int64_t L = M->fL[f], R = M->fR[f];
     for (int k = 0; k < M->fngp[f]; ++k) {
@@ -418,12 +434,16 @@ int orc_residual_fine(orc_solver* S, const double* W, const double* G, const dou
       for (int q = 0; q < 5; ++q) {
         res[5 * L + q] -= w * F[q];
         for (int d = 0; d < 3; ++d) gs[15 * L + 3 * q + d] += Wt[q] * dA[d];
+        g_last_fabs[5 * L + q] += fabs(w * F[q]);
+        g_last_gabs[5 * L + q] += fabs(w * Wt[q]) / M->vol[L];
       }
       al[L] *= gpa[4 * f + k];
       if (R >= 0) {
         for (int q = 0; q < 5; ++q) {
           res[5 * R + q] += w * F[q];
           for (int d = 0; d < 3; ++d) gs[15 * R + 3 * q + d] -= Wt[q] * dA[d];
+          g_last_fabs[5 * R + q] += fabs(w * F[q]);
+          g_last_gabs[5 * R + q] += fabs(w * Wt[q]) / M->vol[R];
         }
         al[R] *= gpa[4 * f + k];
       }
@@ -702,3 +722,15 @@ double* orc_solver_W(orc_solver* S) { return S->W; }
 double* orc_solver_G(orc_solver* S) { return S->G; }
 double* orc_solver_alpha(orc_solver* S) { return S->alpha; }
 int64_t orc_solver_skipped(orc_solver* S) { return S->skipped_corrections; }
+
+/* the term magnitudes of the last fine residual, component-major [5][nc] each (nullable) */
+int orc_solver_term_scales(orc_solver* S, double* fabs_out, double* gabs_out) {
+  const int64_t nc = S->M->nc;
+  if (g_last_n != nc || !g_last_fabs) return -1;
+  for (int64_t i = 0; i < nc; ++i)
+    for (int q = 0; q < 5; ++q) {
+      if (fabs_out) fabs_out[q * nc + i] = g_last_fabs[5 * i + q];
+      if (gabs_out) gabs_out[q * nc + i] = g_last_gabs[5 * i + q];
+    }
+  return 0;
+}

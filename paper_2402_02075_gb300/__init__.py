@@ -1,0 +1,232 @@
+"""Python binding of libcgks (include/cgks.h): multigrid compact gas-kinetic scheme on GB300.
+
+Argument marshalling only: every step of the method runs in the CUDA kernels of libcgks.so.
+Device arrays are torch CUDA tensors (float64, component-major [5][N] / [15][N]); PyTorch provides
+device memory and streams.  The functions named cgks_* mirror the C entry points one to one;
+`Context` is a convenience wrapper over them.  Importing this module does not need a GPU; calling
+into the library does, and it fails loudly when libcgks.so has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcgks.so")
+_lib = None
+
+STATUS = {0: "CGKS_OK", 1: "CGKS_EINVAL", 2: "CGKS_ENOMEM", 3: "CGKS_ECUDA", 4: "CGKS_EMESH", 5: "CGKS_ENAN",
+          6: "CGKS_ENOTCONV", 7: "CGKS_ETIMEOUT", 8: "CGKS_EUNSUPPORTED"}
+
+# every entry point declared in include/cgks.h
+EXPORTS = ["cgks_default_params", "cgks_create", "cgks_destroy", "cgks_set_params", "cgks_mesh_upload",
+           "cgks_level_info", "cgks_coarse_map", "cgks_level_geometry", "cgks_fine_moments", "cgks_state_init",
+           "cgks_state_get", "cgks_residual", "cgks_kfvs_residual", "cgks_step", "cgks_vcycle", "cgks_steady_solve",
+           "cgks_adjoint", "cgks_fp64_peak", "cgks_last_error"]
+
+
+class CgksError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("mach", C.c_double), ("reynolds", C.c_double), ("prandtl", C.c_double),
+                ("aoa", C.c_double * 2), ("cfl_fine", C.c_double), ("cfl_coarse", C.c_double),
+                ("eps_inviscid", C.c_double), ("c_press", C.c_double), ("weno_eps", C.c_double),
+                ("skew_min", C.c_double), ("n_levels", C.c_int32), ("pre", C.c_int32), ("post", C.c_int32),
+                ("coarse_steps", C.c_int32), ("passes_per_level", C.c_int32), ("viscous", C.c_int32),
+                ("dt_mode", C.c_int32), ("precision", C.c_int32), ("agglo_seed", C.c_uint64)]
+
+
+def load(path: str = LIB_PATH):
+    """Load libcgks.so (raises when it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is missing: build it with paper_2402_02075_gb300.build.build()")
+        L = C.CDLL(path)
+        P, d, i32, i64 = C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p
+        sig = {
+            "cgks_default_params": [C.POINTER(Params)],
+            "cgks_create": [C.POINTER(Params), P, C.POINTER(C.c_void_p)],
+            "cgks_destroy": [P],
+            "cgks_set_params": [P, C.POINTER(Params)],
+            "cgks_mesh_upload": [P, C.c_int64, d, C.c_int64, P, i64, i32, C.c_int64, i64, i32, i32, i32, C.c_int64],
+            "cgks_level_info": [P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
+            "cgks_coarse_map": [P, C.c_int, i32],
+            "cgks_level_geometry": [P, C.c_int, d, d, i32, i32, i32, d],
+            "cgks_fine_moments": [P, d],
+            "cgks_state_init": [P, d, d, d],
+            "cgks_state_get": [P, d, d, d],
+            "cgks_residual": [P, C.c_int, d, d, d, d, C.POINTER(C.c_double)],
+            "cgks_kfvs_residual": [P, C.c_int, d, d],
+            "cgks_step": [P, C.c_int, C.POINTER(C.c_double)],
+            "cgks_vcycle": [P, C.c_int, C.POINTER(C.c_double)],
+            "cgks_steady_solve": [P, C.c_int, C.c_double, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_double),
+                                  C.POINTER(C.c_double)],
+            "cgks_adjoint": [P, d, C.c_int, d, d],
+            "cgks_fp64_peak": [C.POINTER(C.c_double)],
+            "cgks_last_error": [P],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = C.c_char_p if name == "cgks_last_error" else C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(status, ctx=None):
+    if status != 0:
+        msg = load().cgks_last_error(ctx)
+        raise CgksError(status, msg.decode() if msg else "")
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    _check(load().cgks_default_params(C.byref(p)))
+    for k, v in kw.items():
+        if k == "aoa":
+            p.aoa[0], p.aoa[1] = v
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _host(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _hp(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+# ---- the C entry points under their own names ----------------------------------------------
+
+def cgks_fp64_peak() -> float:
+    v = C.c_double()
+    _check(load().cgks_fp64_peak(C.byref(v)))
+    return v.value
+
+
+class Context:
+    """One libcgks context bound to the current torch CUDA stream."""
+
+    def __init__(self, params: Params | None = None, stream=None):
+        import torch
+        self.torch = torch
+        self.params = params or default_params()
+        self.stream = stream or torch.cuda.current_stream()
+        h = C.c_void_p()
+        _check(load().cgks_create(C.byref(self.params), C.c_void_p(self.stream.cuda_stream), C.byref(h)))
+        self.h = h
+        self.nc = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().cgks_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def set_params(self, params: Params):
+        _check(load().cgks_set_params(self.h, C.byref(params)), self.h)
+        self.params = params
+
+    def mesh_upload(self, m):
+        xyz = _host(m["xyz"], np.float64)
+        ct = _host(m["cell_type"], np.int8)
+        cp = _host(m["cell_ptr"], np.int64)
+        cn = _host(m["cell_nodes"], np.int32)
+        bp = _host(m["bface_ptr"], np.int64)
+        bn = _host(m["bface_nodes"], np.int32)
+        bt = _host(m["bface_tag"], np.int32)
+        pp = _host(m["periodic_pairs"], np.int32).reshape(-1)
+        _check(load().cgks_mesh_upload(self.h, len(xyz), _hp(xyz), len(ct), _hp(ct), _hp(cp), _hp(cn), len(bt), _hp(bp),
+                                       _hp(bn), _hp(bt), _hp(pp) if len(pp) else None, len(pp) // 2), self.h)
+        self.nc = len(ct)
+
+    def level_info(self, level):
+        nc, nf = C.c_int64(), C.c_int64()
+        _check(load().cgks_level_info(self.h, level, C.byref(nc), C.byref(nf)), self.h)
+        return nc.value, nf.value
+
+    def _empty(self, *shape, dtype=None):
+        t = self.torch
+        return t.empty(*shape, dtype=dtype or t.float64, device="cuda")
+
+    def coarse_map(self, level):
+        n_finer = self.level_info(level - 1)[0]
+        out = self._empty(n_finer, dtype=self.torch.int32)
+        _check(load().cgks_coarse_map(self.h, level, _ptr(out)), self.h)
+        return out
+
+    def level_geometry(self, level):
+        nc, nf = self.level_info(level)
+        t = self.torch
+        vol, ctr = self._empty(nc), self._empty(3, nc)
+        fL, fR, tag = (self._empty(nf, dtype=t.int32) for _ in range(3))
+        Sn = self._empty(3, nf)
+        _check(load().cgks_level_geometry(self.h, level, _ptr(vol), _ptr(ctr), _ptr(fL), _ptr(fR), _ptr(tag), _ptr(Sn)),
+               self.h)
+        return dict(vol=vol, ctr=ctr, fL=fL, fR=fR, tag=tag, Sn=Sn)
+
+    def fine_moments(self):
+        m2 = self._empty(6, self.nc)
+        _check(load().cgks_fine_moments(self.h, _ptr(m2)), self.h)
+        return m2
+
+    def state_init(self, W, G=None, alpha=None):
+        for x in (W, G, alpha):
+            assert x is None or (x.is_cuda and x.dtype == self.torch.float64 and x.is_contiguous())
+        _check(load().cgks_state_init(self.h, _ptr(W), _ptr(G), _ptr(alpha)), self.h)
+
+    def state_get(self):
+        W, G, a = self._empty(5, self.nc), self._empty(15, self.nc), self._empty(self.nc)
+        _check(load().cgks_state_get(self.h, _ptr(W), _ptr(G), _ptr(a)), self.h)
+        return W, G, a
+
+    def residual(self, order=3, grads=True):
+        res, dt = self._empty(5, self.nc), self._empty(self.nc)
+        G = self._empty(15, self.nc) if (grads and order == 3) else None
+        a = self._empty(self.nc) if (grads and order == 3) else None
+        nm = C.c_double()
+        _check(load().cgks_residual(self.h, order, _ptr(res), _ptr(G), _ptr(a), _ptr(dt), C.byref(nm)), self.h)
+        return dict(res=res, grad=G, alpha=a, dt=dt, norm=nm.value)
+
+    def kfvs_residual(self, level, W):
+        res = self.torch.empty_like(W)
+        _check(load().cgks_kfvs_residual(self.h, level, _ptr(W), _ptr(res)), self.h)
+        return res
+
+    def step(self, n=1, history=True):
+        h = np.zeros(max(n, 1))
+        _check(load().cgks_step(self.h, n, h.ctypes.data_as(C.POINTER(C.c_double)) if history else None), self.h)
+        return h[:n]
+
+    def vcycle(self, n=1, history=True):
+        h = np.zeros(max(n, 1))
+        _check(load().cgks_vcycle(self.h, n, h.ctypes.data_as(C.POINTER(C.c_double)) if history else None), self.h)
+        return h[:n]
+
+    def steady_solve(self, multigrid=True, drop=1e-10, max_iters=100000, raise_on_notconv=True):
+        it, fd, sec = C.c_int64(), C.c_double(), C.c_double()
+        s = load().cgks_steady_solve(self.h, int(bool(multigrid)), drop, max_iters, C.byref(it), C.byref(fd), C.byref(sec))
+        if s != 6 or raise_on_notconv:
+            _check(s, self.h)
+        return dict(iters=it.value, drop=fd.value, seconds=sec.value, converged=s == 0)
+
+
+def upload_mesh(mesh, params=None):
+    """Convenience: a Context with `mesh` (a meshgen-style dict of host arrays) uploaded."""
+    ctx = Context(params)
+    ctx.mesh_upload(mesh)
+    return ctx

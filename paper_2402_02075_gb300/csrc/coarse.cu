@@ -1,0 +1,255 @@
+// Coarse levels of the V-cycle (Sec. 4.2 of the paper): first-order KFVS residual, local time
+// steps, FAS forcing and forward-Euler smoothing, volume-weighted state restriction, summed
+// residual restriction, injection correction, and the residual norm.  All sums run in a fixed
+// order (no floating-point atomics), so results are bitwise reproducible.
+#include "internal.cuh"
+#include "kinetic.cuh"
+
+__global__ void k_kfvs_faces(int64_t nf, const int32_t* __restrict__ fL, const int32_t* __restrict__ fR,
+                             const int32_t* __restrict__ ftag, const double* __restrict__ Sn, int64_t nc,
+                             const double* __restrict__ W, double* __restrict__ ff, Phys ph, DevErr* err) {
+  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= nf) return;
+  const double S[3] = {Sn[f], Sn[nf + f], Sn[2 * nf + f]};
+  const double s = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+  const double n[3] = {S[0] / s, S[1] / s, S[2] / s};
+  const int64_t L = fL[f], R = fR[f];
+  double WL[5], WR[5], F[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) WL[q] = W[q * nc + L];
+  if (R >= 0) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) WR[q] = W[q * nc + R];
+  } else if (!bc_ghost<double>(ftag[f], n, WL, nullptr, WR, nullptr, ph.gamma, ph.Winf)) {
+    set_err(err, CGKS_ENAN, (int)L, 20);
+  }
+  if (!kfvs_flux<double>(WL, WR, n, ph.K, ph.gamma - 1.0, F)) set_err(err, CGKS_ENAN, (int)L, 21);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) ff[q * nf + f] = s * F[q];
+}
+
+// res = -(sum of outward face fluxes); optional forcing F and explicit update W += dt/V (res + F)
+__global__ void k_kfvs_gather(int64_t nc, int64_t nf, const int32_t* __restrict__ ptr, const int32_t* __restrict__ c2f,
+                              const int32_t* __restrict__ fL, const int32_t* __restrict__ fR,
+                              const double* __restrict__ ff, double* __restrict__ res) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  double r[5] = {0, 0, 0, 0, 0};
+  for (int32_t k = ptr[c]; k < ptr[c + 1]; ++k) {
+    const int64_t f = c2f[k];
+    const int32_t a = fL[f], b = fR[f];
+    if (a == b) continue;  // a cell's periodic image of itself: the two sides cancel
+    const double s = a == c ? 1.0 : -1.0;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) r[q] -= s * ff[q * nf + f];
+  }
+#pragma unroll
+  for (int q = 0; q < 5; ++q) res[q * nc + c] = r[q];
+}
+
+__global__ void k_coarse_dt(int64_t nc, int64_t nf, const int32_t* __restrict__ ptr, const int32_t* __restrict__ c2f,
+                            const double* __restrict__ Sn, const double* __restrict__ vol, const double* __restrict__ W,
+                            double* __restrict__ dt, double gamma, double cfl) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  const double r = 1.0 / W[c];
+  const double u[3] = {W[nc + c] * r, W[2 * nc + c] * r, W[3 * nc + c] * r};
+  const double p = (gamma - 1.0) * (W[4 * nc + c] - 0.5 * W[c] * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
+  const double snd = sqrt(gamma * p * r);
+  double s = 0.0;
+  for (int32_t k = ptr[c]; k < ptr[c + 1]; ++k) {
+    const int64_t f = c2f[k];
+    const double S[3] = {Sn[f], Sn[nf + f], Sn[2 * nf + f]};
+    const double a = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+    s += fabs(u[0] * S[0] + u[1] * S[1] + u[2] * S[2]) + a * snd;
+  }
+  dt[c] = cfl * vol[c] / s;
+}
+
+// F = Rs - R  (FAS forcing term)
+__global__ void k_forcing(int64_t n5, const double* __restrict__ Rs, const double* __restrict__ R, double* __restrict__ F) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j < n5) F[j] = Rs[j] - R[j];
+}
+
+// W += dt / V (R + F)
+__global__ void k_fe_update(int64_t nc, const double* __restrict__ dt, const double* __restrict__ vol,
+                            const double* __restrict__ R, const double* __restrict__ F, double* __restrict__ W,
+                            double gamma, DevErr* err) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  const double h = dt[c] / vol[c];
+  double w[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    w[q] = W[q * nc + c] + h * (R[q * nc + c] + F[q * nc + c]);
+    W[q * nc + c] = w[q];
+  }
+  const double p = (gamma - 1.0) * (w[4] - 0.5 * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]) / w[0]);
+  if (!(w[0] > 0.0) || !(p > 0.0) || !isfinite(p)) set_err(err, CGKS_ENAN, (int)c, 22);
+}
+
+// coarse state = sum V_i W_i / V_c and coarse defect = sum (R_i [+ F_i]) over the finer cells of
+// each coarse cell, in ascending finer-cell order
+__global__ void k_restrict(int64_t ncc, int64_t ncf, const int32_t* __restrict__ aptr, const int32_t* __restrict__ agg,
+                           const double* __restrict__ vf, const double* __restrict__ vc, const double* __restrict__ Wf,
+                           const double* __restrict__ Rf, const double* __restrict__ Ff, double* __restrict__ Wc,
+                           double* __restrict__ Rc) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= ncc) return;
+  double w[5] = {0, 0, 0, 0, 0}, r[5] = {0, 0, 0, 0, 0};
+  for (int32_t k = aptr[c]; k < aptr[c + 1]; ++k) {
+    const int64_t i = agg[k];
+    const double v = vf[i];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      w[q] += v * Wf[q * ncf + i];
+      r[q] += Ff ? Rf[q * ncf + i] + Ff[q * ncf + i] : Rf[q * ncf + i];
+    }
+  }
+  const double rv = 1.0 / vc[c];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    Wc[q * ncc + c] = w[q] * rv;
+    Rc[q * ncc + c] = r[q];
+  }
+}
+
+// W_f += W_c - W_c^0 (injection); a correction that would make rho or p non-positive is skipped
+__global__ void k_prolong(int64_t ncf, int64_t ncc, const int32_t* __restrict__ f2c, const double* __restrict__ Wc,
+                          const double* __restrict__ Wc0, double* __restrict__ Wf, double gamma,
+                          unsigned long long* skipped) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= ncf) return;
+  const int64_t c = f2c[i];
+  double w[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) w[q] = Wf[q * ncf + i] + (Wc[q * ncc + c] - Wc0[q * ncc + c]);
+  const double p = (gamma - 1.0) * (w[4] - 0.5 * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]) / w[0]);
+  if (w[0] > 0.0 && p > 0.0) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) Wf[q * ncf + i] = w[q];
+  } else {
+    atomicAdd(skipped, 1ULL);
+  }
+}
+
+// sqrt(mean (res_rho / V)^2): per-block partial sums, then one thread adds them in block order
+__global__ void k_norm_partial(int64_t n, const double* __restrict__ res, const double* __restrict__ vol,
+                               double* __restrict__ part) {
+  __shared__ double s[256];
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = res[i] / vol[i];
+    acc += x * x;
+  }
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if (threadIdx.x < k) s[threadIdx.x] += s[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+}
+
+__global__ void k_norm_final(int nparts, int64_t n, const double* __restrict__ part, double* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = 0.0;
+  for (int k = 0; k < nparts; ++k) s += part[k];
+  *out = sqrt(s / (double)n);
+}
+
+cgks_status density_norm(cgks_ctx* ctx, const double* res, const double* vol, int64_t n, double* out_dev) {
+  const int parts = 304;
+  k_norm_partial<<<parts, 256, 0, ctx->stream>>>(n, res, vol, ctx->nrm_part);
+  k_norm_final<<<1, 32, 0, ctx->stream>>>(parts, n, ctx->nrm_part, out_dev);
+  CK(cudaGetLastError());
+  return CGKS_OK;
+}
+
+cgks_status global_min_dt(cgks_ctx* ctx, double* dt, int64_t n);
+
+cgks_status kfvs_residual(cgks_ctx* ctx, int lev, const double* W, double* res) {
+  const Level& L = ctx->L[lev];
+  const Phys ph = make_phys(ctx->P);
+  double* ff = lev == 0 ? ctx->ffl : ctx->C[lev].ff;
+  k_kfvs_faces<<<grid_for(L.nf, 256), 256, 0, ctx->stream>>>(L.nf, L.fL, L.fR, L.ftag, L.Sn, L.nc, W, ff, ph, ctx->derr);
+  k_kfvs_gather<<<grid_for(L.nc, 256), 256, 0, ctx->stream>>>(L.nc, L.nf, L.c2f_ptr, L.c2f, L.fL, L.fR, ff, res);
+  CK(cudaGetLastError());
+  return CGKS_OK;
+}
+
+cgks_status coarse_dt(cgks_ctx* ctx, int lev, const double* W, double* dt) {
+  const Level& L = ctx->L[lev];
+  k_coarse_dt<<<grid_for(L.nc, 256), 256, 0, ctx->stream>>>(L.nc, L.nf, L.c2f_ptr, L.c2f, L.Sn, L.vol, W, dt,
+                                                            ctx->P.gamma, ctx->P.cfl_coarse);
+  if (ctx->P.dt_mode == 1) CKS(global_min_dt(ctx, dt, L.nc));
+  CK(cudaGetLastError());
+  return CGKS_OK;
+}
+
+// coarse-level FAS smoothing on level l with the restricted state already in C[l].W (and W0) and
+// the restricted defect in C[l].Rs, then recursion to the next level and correction
+static cgks_status coarse_cycle(cgks_ctx* ctx, int l) {
+  const Level& L = ctx->L[l];
+  CoarseBuf& B = ctx->C[l];
+  cudaStream_t st = ctx->stream;
+  const int64_t n5 = 5 * L.nc;
+  CKS(kfvs_residual(ctx, l, B.W, B.R));
+  k_forcing<<<grid_for(n5, 256), 256, 0, st>>>(n5, B.Rs, B.R, B.F);
+  for (int s = 0; s < ctx->P.coarse_steps; ++s) {
+    CKS(kfvs_residual(ctx, l, B.W, B.R));
+    CKS(coarse_dt(ctx, l, B.W, B.dt));
+    k_fe_update<<<grid_for(L.nc, 256), 256, 0, st>>>(L.nc, B.dt, L.vol, B.R, B.F, B.W, ctx->P.gamma, ctx->derr);
+  }
+  if (l + 1 < (int)ctx->L.size()) {
+    const Level& Cn = ctx->L[l + 1];
+    CoarseBuf& N = ctx->C[l + 1];
+    CKS(kfvs_residual(ctx, l, B.W, B.R));
+    k_restrict<<<grid_for(Cn.nc, 256), 256, 0, st>>>(Cn.nc, L.nc, Cn.agg_ptr, Cn.agg, L.vol, Cn.vol, B.W, B.R, B.F,
+                                                     N.W, N.Rs);
+    CK(cudaMemcpyAsync(N.W0, N.W, sizeof(double) * 5 * Cn.nc, cudaMemcpyDeviceToDevice, st));
+    CKS(coarse_cycle(ctx, l + 1));
+    k_prolong<<<grid_for(L.nc, 256), 256, 0, st>>>(L.nc, Cn.nc, Cn.f2c, N.W, N.W0, B.W, ctx->P.gamma,
+                                                   (unsigned long long*)ctx->d_count);
+    for (int s = 0; s < ctx->P.post; ++s) {
+      CKS(kfvs_residual(ctx, l, B.W, B.R));
+      CKS(coarse_dt(ctx, l, B.W, B.dt));
+      k_fe_update<<<grid_for(L.nc, 256), 256, 0, st>>>(L.nc, B.dt, L.vol, B.R, B.F, B.W, ctx->P.gamma, ctx->derr);
+    }
+  }
+  CK(cudaGetLastError());
+  return CGKS_OK;
+}
+
+// one explicit CGKS step of the fine level (Eq. smo); norm of the residual before the step
+cgks_status step_once(cgks_ctx* ctx, double* norm_dev) {
+  CKS(fine_fluxes(ctx, ctx->W, ctx->G, ctx->alpha));
+  // the gather reads only the Gauss-point records, so W, gradW and alpha are updated in place
+  CKS(fine_gather(ctx, ctx->W, ctx->W, ctx->res, ctx->G, ctx->alpha, 1));
+  if (norm_dev) CKS(density_norm(ctx, ctx->res, ctx->F.vol, ctx->F.nc, norm_dev));
+  return CGKS_OK;
+}
+
+// one V-cycle (Sec. 4.2)
+cgks_status vcycle_once(cgks_ctx* ctx, double* norm_dev) {
+  cudaStream_t st = ctx->stream;
+  const int pre = ctx->P.pre > 0 ? ctx->P.pre : 1;
+  for (int s = 0; s < pre; ++s) CKS(step_once(ctx, s == 0 ? norm_dev : nullptr));
+  if (ctx->L.size() <= 1) return CGKS_OK;
+  const Fine& F = ctx->F;
+  const Level& C1 = ctx->L[1];
+  CoarseBuf& B1 = ctx->C[1];
+  // defect at the smoothed state (gradient and compression outputs discarded)
+  CKS(fine_fluxes(ctx, ctx->W, ctx->G, ctx->alpha));
+  CKS(fine_gather(ctx, ctx->W, nullptr, ctx->res, nullptr, nullptr, 0));
+  k_restrict<<<grid_for(C1.nc, 256), 256, 0, st>>>(C1.nc, F.nc, C1.agg_ptr, C1.agg, F.vol, C1.vol, ctx->W, ctx->res,
+                                                   nullptr, B1.W, B1.Rs);
+  CK(cudaMemcpyAsync(B1.W0, B1.W, sizeof(double) * 5 * C1.nc, cudaMemcpyDeviceToDevice, st));
+  CKS(coarse_cycle(ctx, 1));
+  k_prolong<<<grid_for(F.nc, 256), 256, 0, st>>>(F.nc, C1.nc, C1.f2c, B1.W, B1.W0, ctx->W, ctx->P.gamma,
+                                                 (unsigned long long*)ctx->d_count);
+  for (int s = 0; s < ctx->P.post; ++s) CKS(step_once(ctx, nullptr));
+  CK(cudaGetLastError());
+  return CGKS_OK;
+}

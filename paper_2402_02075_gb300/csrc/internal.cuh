@@ -1,0 +1,151 @@
+// Internal declarations of libcgks: device buffers of the mesh hierarchy and the solver state,
+// launch helpers and error plumbing.  Not part of the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "cgks.h"
+
+#define CGKS_MAXNF 6          // faces of a hexahedron
+#define CGKS_KOP 216          // reconstruction operator entries per cell: 9 x (4 * 6)
+#define CGKS_RC 50            // reconstruction coefficients per cell: 5 variables x 10
+#define CGKS_AUX 8            // per-cell constants of the smoothness indicators
+#define CGKS_AGG_CAP 256      // records per coarse cell while building coarse faces
+#define HD __host__ __device__ __forceinline__
+
+// device error word: [0] code (cgks_status), [1] cell or face index, [2] detail
+struct DevErr {
+  int32_t code, index, detail, pad;
+};
+
+__host__ __device__ __forceinline__ void set_err(DevErr* e, int code, int index, int detail = 0) {
+#ifdef __CUDA_ARCH__
+  if (atomicCAS(&e->code, 0, code) == 0) {
+#else
+  if (e->code == 0) {
+    e->code = code;
+#endif
+    e->index = index;
+    e->detail = detail;
+  }
+}
+
+// constants of the physical model passed by value to the kernels
+struct Phys {
+  double gamma, K, mu, prandtl, eps_inviscid, c_press, weno_eps, cfl_fine, cfl_coarse;
+  int viscous, dt_mode;
+  double Winf[5];
+};
+
+// one level of the multigrid hierarchy as used by the first-order solver and by the coarsening
+struct Level {
+  int64_t nc = 0, nf = 0, n_int = 0, n_per = 0;
+  double *vol = nullptr, *ctr = nullptr;                          // [nc], [3][nc]
+  int32_t *fL = nullptr, *fR = nullptr, *ftag = nullptr, *ftagR = nullptr;  // [nf]
+  double *Sn = nullptr, *area = nullptr, *amom = nullptr, *shift = nullptr;  // [3][nf],[nf],[3][nf],[3][nf]
+  int32_t *c2f_ptr = nullptr, *c2f = nullptr;                    // cell -> faces, ascending ids
+  int32_t *f2c = nullptr;                                        // finer cell -> this level's cell
+  int64_t nc_finer = 0;
+  int32_t *agg_ptr = nullptr, *agg = nullptr;                    // this level's cell -> finer cells
+};
+
+// the fine mesh with its Gauss points and reconstruction operators
+struct Fine {
+  int64_t nc = 0, nf = 0, n_int = 0, n_per = 0, n_bnd = 0, ngp = 0;
+  int8_t* ctype = nullptr;
+  double *vol = nullptr, *ctr = nullptr, *m2 = nullptr;          // [nc], [3][nc], [6][nc]
+  int32_t *fL = nullptr, *fR = nullptr, *ftag = nullptr, *ftagR = nullptr, *flf = nullptr;
+  int32_t *gp_ptr = nullptr, *gp_face = nullptr;                 // [nf + 1], [ngp]
+  double *gp_x = nullptr, *gp_A = nullptr;                       // [3][ngp] point, area vector
+  double *fshift = nullptr, *fnrm = nullptr, *fctr = nullptr;    // [3][nf] each
+  int32_t *cf = nullptr;                                         // [6][nc] face of each local face
+  int8_t* cside = nullptr;                                       // [6][nc] 0: cell is L, 1: R
+  int32_t *c2f_ptr = nullptr, *c2f = nullptr;                    // cell -> faces (ascending)
+  double *Kop = nullptr;                                         // [216][nc] p^2 operator
+  double *ggw = nullptr;                                         // [18][nc] outward S n / (2|Omega|)
+  double *lsw = nullptr;                                         // [18][nc] least-squares gradient weights
+  double *aux = nullptr;                                         // [8][nc] |Omega|^(2/3), |Omega|^(4/3), m2
+  double *dtw = nullptr;                                         // [24][nc] time-step weights per local face
+};
+
+struct CoarseBuf {  // per coarse level work arrays
+  double *W = nullptr, *W0 = nullptr, *Rs = nullptr, *F = nullptr, *R = nullptr, *dt = nullptr, *ff = nullptr;
+};
+
+struct cgks_ctx {
+  cgks_params P{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  std::string err;
+  bool has_mesh = false, has_state = false;
+  Fine F;
+  std::vector<Level> L;  // L[0] is the fine level seen as a first-order mesh
+  std::vector<CoarseBuf> C;
+  // fine state and work arrays
+  double *W = nullptr, *G = nullptr, *alpha = nullptr;
+  double *rc = nullptr, *dt = nullptr, *res = nullptr;
+  double *gpF = nullptr, *gpW = nullptr, *gpa = nullptr;
+  double *W1 = nullptr;             // copy of W used by the V-cycle
+  double *ffl = nullptr;            // first-order face fluxes of level 0
+  double *nrm_part = nullptr, *nrm = nullptr, *h_nrm = nullptr;
+  DevErr* derr = nullptr;
+  DevErr* h_err = nullptr;
+  int64_t* d_count = nullptr;
+  int64_t* h_count = nullptr;
+  double r1 = 0.0;
+  int64_t iters = 0;
+  std::vector<void*> mesh_allocs;   // freed on re-upload / destroy
+  std::vector<void*> ctx_allocs;    // freed on destroy
+};
+
+// ---- error helpers (host) ---------------------------------------------------------------------
+cgks_status cgks_fail(cgks_ctx* c, cgks_status s, const std::string& msg);
+#define CK(call)                                                                                   \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) return cgks_fail(ctx, CGKS_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+#define CKS(expr)                         \
+  do {                                    \
+    cgks_status s_ = (expr);              \
+    if (s_ != CGKS_OK) return s_;         \
+  } while (0)
+
+// device allocation recorded in `list` (zero-filled)
+cgks_status dev_alloc(cgks_ctx* ctx, std::vector<void*>& list, void** p, size_t bytes);
+template <typename T>
+cgks_status dalloc(cgks_ctx* ctx, std::vector<void*>& list, T** p, size_t count) {
+  return dev_alloc(ctx, list, reinterpret_cast<void**>(p), sizeof(T) * (count ? count : 1));
+}
+void free_list(std::vector<void*>& list);
+
+inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
+
+// exclusive prefix sum of n int32 values (device), total returned through *total (host) when
+// non-null (synchronises).  Uses ctx scratch allocated on demand.
+cgks_status scan_exclusive(cgks_ctx* ctx, const int32_t* in, int32_t* out, int64_t n, int64_t* total);
+
+// entry points between translation units
+cgks_status build_fine_mesh(cgks_ctx* ctx, int64_t n_nodes, const double* xyz, int64_t n_cells, const int8_t* ctype,
+                            const int64_t* cell_ptr, const int32_t* cell_nodes, int64_t n_bfaces,
+                            const int64_t* bface_ptr, const int32_t* bface_nodes, const int32_t* bface_tag,
+                            const int32_t* periodic_pairs, int64_t n_periodic);
+cgks_status build_levels(cgks_ctx* ctx);
+Phys make_phys(const cgks_params& P);
+cgks_status check_device_error(cgks_ctx* ctx, const char* where);
+
+// fine CGKS residual: reconstruct + Gauss-point fluxes; then either a gather into outputs or an
+// explicit update of (W, G, alpha)
+cgks_status fine_fluxes(cgks_ctx* ctx, const double* W, const double* G, const double* alpha);
+cgks_status fine_gather(cgks_ctx* ctx, const double* W_in, double* W_out, double* res, double* G_out,
+                        double* alpha_out, int update);
+cgks_status density_norm(cgks_ctx* ctx, const double* res, const double* vol, int64_t n, double* out_dev);
+
+// first-order (KFVS) residual of a level; res may equal nullptr when only the face fluxes are needed
+cgks_status kfvs_residual(cgks_ctx* ctx, int lev, const double* W, double* res);
+cgks_status coarse_dt(cgks_ctx* ctx, int lev, const double* W, double* dt);
+cgks_status vcycle_once(cgks_ctx* ctx, double* norm_dev);
+cgks_status step_once(cgks_ctx* ctx, double* norm_dev);

@@ -1,0 +1,174 @@
+"""Explicit steps, coarsening, coarse levels and V-cycles of the CUDA library against the oracle,
+plus determinism and the error paths of the C ABI."""
+import numpy as np
+import pytest
+
+import meshgen as mg
+from parity import assert_normwise
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def cg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2402_02075_gb300 as cg
+    from paper_2402_02075_gb300 import build
+    build.build()
+    return cg
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _pair(cg, orc, mesh, W, G, **prm):
+    ctx = cg.upload_mesh(mesh, cg.default_params(**prm))
+    ctx.state_init(_t(W), _t(G))
+    om = orc.Mesh(mesh)
+    os_ = orc.Solver(om, orc.params(**prm))
+    os_.set_state(W, G)
+    return ctx, om, os_
+
+
+def _compare_states(ctx, os_, atol_w=1e-11, rtol_g=1e-10):
+    """States after iterations: each step adds dt/|Omega| x residual, and the residuals agree to
+    1e-11 of the summed flux magnitudes, so W agrees to 1e-11 of its scale."""
+    Wg, Gg, ag = (x.cpu().numpy() for x in ctx.state_get())
+    Wo, Go, ao = os_.state()
+    assert np.abs(Wg - Wo).max() <= atol_w * np.abs(Wo).max(), np.abs(Wg - Wo).max()
+    assert np.abs(Gg - Go).max() <= rtol_g * np.abs(Go).max(), np.abs(Gg - Go).max()
+    assert np.abs(ag - ao).max() <= 1e-12
+
+
+def test_config1_hundred_steps(cg, orc):
+    """The 16^3 mixed periodic density wave (6,912 cells), global time step, CFL 0.5, 100 steps."""
+    mesh = mg.periodic_box(16)
+    W, G = mg.density_wave_state(mesh)
+    ctx, om, os_ = _pair(cg, orc, mesh, W, G, mach=0.2, dt_mode=1, cfl_fine=0.5, n_levels=1)
+    hg = ctx.step(100)
+    ho = os_.run(100)
+    np.testing.assert_allclose(hg, ho, rtol=1e-9)
+    _compare_states(ctx, os_)
+
+
+@pytest.mark.parametrize("name,mk,seed", [
+    ("periodic8", lambda: mg.periodic_box(8), 0),
+    ("periodic8-s3", lambda: mg.periodic_box(8), 3),
+    ("wall", lambda: mg.wall_box(16, 8, 16, n_prism=6), 0),
+    ("ramp", lambda: mg.ramp_box(24, 12, 8, n_prism=3), 0),
+    ("scale10", lambda: mg.scale_box(10), 1),
+])
+def test_coarsening_is_bit_exact(cg, orc, name, mk, seed):
+    mesh = mk()
+    prm = dict(n_levels=3, agglo_seed=seed)
+    ctx = cg.upload_mesh(mesh, cg.default_params(**prm))
+    om = orc.Mesh(mesh)
+    os_ = orc.Solver(om, orc.params(**prm))
+    for lev in (1, 2):
+        Lo = os_.level(lev)
+        nc, nf = ctx.level_info(lev)
+        assert (nc, nf) == (Lo["nc"], Lo["nf"])
+        assert np.array_equal(ctx.coarse_map(lev).cpu().numpy(), Lo["map"])
+        g = ctx.level_geometry(lev)
+        assert np.array_equal(g["fL"].cpu().numpy(), Lo["fL"])
+        assert np.array_equal(g["fR"].cpu().numpy(), Lo["fR"])
+        assert np.array_equal(g["tag"].cpu().numpy(), Lo["tag"])
+        assert_normwise(g["vol"].cpu().numpy()[None], Lo["vol"][None], 1e-13, "coarse volumes")
+        assert_normwise(g["ctr"].cpu().numpy(), Lo["ctr"].T, 1e-13, "coarse centroids")
+        assert_normwise(g["Sn"].cpu().numpy(), Lo["Sn"].T, 1e-12, "coarse area vectors",
+                        scale=np.full((3, 1), np.abs(Lo["Sn"]).max()))
+
+
+@pytest.mark.parametrize("mk", [lambda: mg.periodic_box(8), lambda: mg.wall_box(16, 8, 16, n_prism=6),
+                                lambda: mg.ramp_box(24, 12, 8, n_prism=3)])
+def test_coarse_kfvs_residuals(cg, orc, mk):
+    mesh = mk()
+    prm = dict(n_levels=3, mach=0.6)
+    ctx = cg.upload_mesh(mesh, cg.default_params(**prm))
+    om = orc.Mesh(mesh)
+    os_ = orc.Solver(om, orc.params(**prm))
+    rng = np.random.default_rng(3)
+    for lev in (0, 1, 2):
+        n = ctx.level_info(lev)[0]
+        W, _ = mg.uniform_state(n, mach=0.6)
+        W = W * (1 + 0.03 * rng.standard_normal(W.shape))
+        got = ctx.kfvs_residual(lev, _t(W)).cpu().numpy()
+        ref = os_.kfvs_residual(lev, W)
+        assert_normwise(got, ref, 1e-12, f"KFVS residual level {lev}")
+
+
+@pytest.mark.parametrize("case", ["wave", "wall", "ramp"])
+def test_vcycles(cg, orc, case):
+    rng = np.random.default_rng(11)
+    if case == "wave":
+        mesh = mg.periodic_box(8)
+        W, G = mg.density_wave_state(mesh)
+        prm = dict(mach=0.2)
+        n = 4
+    elif case == "wall":
+        mesh = mg.wall_box(16, 8, 16, n_prism=6)
+        W, G = mg.uniform_state(len(mesh["cell_type"]), mach=0.5)
+        prm = dict(mach=0.5, viscous=1, reynolds=1e4, prandtl=0.72)
+        n = 3
+    else:
+        mesh = mg.ramp_box(24, 12, 8, n_prism=3)
+        W, G = mg.uniform_state(len(mesh["cell_type"]), mach=3.0)
+        prm = dict(mach=3.0)
+        n = 3
+    ctx, om, os_ = _pair(cg, orc, mesh, W, G, n_levels=3, **prm)
+    hg = ctx.vcycle(n)
+    ho = os_.run(n, multigrid=True)
+    np.testing.assert_allclose(hg, ho, rtol=1e-9)
+    _compare_states(ctx, os_)
+
+
+def test_runs_are_bitwise_reproducible(cg):
+    mesh = mg.periodic_box(8)
+    W, G = mg.density_wave_state(mesh)
+    outs = []
+    for _ in range(2):
+        ctx = cg.upload_mesh(mesh, cg.default_params(mach=0.2))
+        ctx.state_init(_t(W), _t(G))
+        h = ctx.vcycle(3)
+        outs.append((h, [x.cpu().numpy() for x in ctx.state_get()]))
+        ctx.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    for a, b in zip(outs[0][1], outs[1][1]):
+        assert np.array_equal(a, b)
+
+
+def test_error_paths(cg):
+    with pytest.raises(cg.CgksError) as e:
+        cg.Context(cg.default_params(gamma=0.9))
+    assert e.value.status == 1
+    with pytest.raises(cg.CgksError) as e:
+        cg.Context(cg.default_params(precision=1))
+    assert e.value.status == 8
+    mesh = mg.periodic_box(4)
+    ctx = cg.Context(cg.default_params())
+    with pytest.raises(cg.CgksError) as e:
+        ctx.step(1)
+    assert e.value.status == 1  # no mesh
+    broken = dict(mesh)
+    broken["bface_tag"] = mesh["bface_tag"][:-2].copy()
+    broken["bface_ptr"] = mesh["bface_ptr"][:-2].copy()
+    broken["periodic_pairs"] = mesh["periodic_pairs"][:-1].copy()
+    with pytest.raises(cg.CgksError) as e:
+        ctx.mesh_upload(broken)
+    assert e.value.status in (1, 4)
+    ctx.mesh_upload(mesh)
+    with pytest.raises(cg.CgksError) as e:
+        ctx.residual()
+    assert e.value.status == 1  # no state
+    W, G = mg.uniform_state(ctx.nc)
+    W[0, 5] = -1.0
+    ctx.state_init(_t(W), _t(G))
+    with pytest.raises(cg.CgksError) as e:
+        ctx.step(1)
+    assert e.value.status == 5 and "index" in str(e.value)
+    assert cg.load().cgks_adjoint(ctx.h, None, 0, None, None) == 8
+    ctx.close()
