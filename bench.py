@@ -1,0 +1,301 @@
+#!/usr/bin/env python3
+"""Benchmark of the multigrid CGKS hot path on one GB300 (or N replicas).
+
+A step is one 3-level V-cycle (Sec. 4.2 of the paper: a CGKS pre-smoothing step, the defect at the
+new state, KFVS forward-Euler smoothing with FAS forcing on the two agglomerated levels, injection
+correction) on the laminar boundary-layer box: 96 x 64 x 64 grid split into 35 wall layers of prisms
+and Kuhn tetrahedra above (1,499,136 cells), no-slip wall, farfield, Mach 0.5, Re 1e4, Pr 0.72,
+seeded synthetic mesh and free-stream start.  The metric is fine cells x V-cycles per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU: one process per GPU (torchrun); each rank runs an independent replica (the method is
+not partitioned in this build), the step time is the maximum over ranks and the value counts the
+cells of all replicas.  --impl reference times the CPU oracle (the plain C implementation used by
+the tests) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mcell-iters/s; wall time to 1e-10 residual drop: FP64 vs mixed V-cycle"
+UNIT = "Mcell-iters/s"
+WORKLOAD = dict(nx=96, ny=64, nz=64, n_prism=35)
+PARAMS = dict(mach=0.5, reynolds=1e4, prandtl=0.72, gamma=1.4, viscous=1, n_levels=3, cfl_fine=0.5,
+              cfl_coarse=0.5, agglo_seed=0)
+# bounded sample of the same workload for the CPU oracle: the same layout and physics at 32 x 24 x 24
+# with 13 prism layers (70,656 cells)
+SAMPLE = dict(nx=32, ny=24, nz=24, n_prism=13)
+# FP64 floating-point operations per Gauss point of the gas-kinetic flux kernel (2 per DFMA, 1 per
+# DADD/DMUL), from the ncu instruction counts of a full capture of the kernel on the 48x32x32 box;
+# the kernel's own arithmetic, all of which the method needs
+FLOP_PER_GP = 5026.7
+# DRAM bytes (read + write) per Gauss point of the same kernel from the same capture (None when the
+# kernel has changed since)
+DRAM_BYTES_PER_GP = 192.7
+
+
+def workload_name(w):
+    cells = w["nx"] * w["ny"] * (2 * w["n_prism"] + 6 * (w["nz"] - w["n_prism"]))
+    return (f"3-level FP64 V-cycle, laminar boundary-layer box {w['nx']}x{w['ny']}x{w['nz']} "
+            f"({cells:,} cells: {w['n_prism']} prism layers + Kuhn tetrahedra), M 0.5, Re 1e4, Pr 0.72")
+
+
+def launches_per_vcycle(P, history=False):
+    """Kernels launched by one V-cycle (fine step, defect, restriction, coarse FAS levels, corrections)."""
+    dtm = 2 if P["dt_mode"] == 1 else 0
+    fine_step = 3 + dtm + (2 if history else 0)
+    n = fine_step * max(P["pre"], 1)
+    nl = P["n_levels"]
+    if nl > 1:
+        n += 3 + dtm + 1  # defect (reconstruct, points, gather) + restriction
+
+        def coarse(l):
+            k = 2 + 1 + P["coarse_steps"] * (2 + 1 + dtm + 1)
+            if l + 1 < nl:
+                k += 2 + 1 + coarse(l + 1) + 1 + P["post"] * (2 + 1 + dtm + 1)
+            return k
+        n += coarse(1) + 1 + P["post"] * fine_step
+    return n
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None:
+            return None
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_baseline(steps_per_sample=2):
+    """The oracle (as it stands) on a bounded sample of the workload: V-cycles per second x cells."""
+    import meshgen as mg
+    import oracle
+    oracle.build()
+    mesh = mg.wall_box(**SAMPLE)
+    M = oracle.Mesh(mesh)
+    prm = oracle.params(**PARAMS)
+    S = oracle.Solver(M, prm)
+    W, G = mg.uniform_state(M.nc, mach=PARAMS["mach"])
+    S.set_state(W, G)
+    S.run(1, multigrid=True)  # warm-up (first touch of the work arrays)
+    t0 = time.perf_counter()
+    S.run(steps_per_sample, multigrid=True)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": M.nc * steps_per_sample / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps_per_sample} V-cycles of the same layout and physics at "
+                      f"{SAMPLE['nx']}x{SAMPLE['ny']}x{SAMPLE['nz']} ({M.nc:,} cells), after 1 warm-up cycle",
+            "seconds": dt}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import meshgen as mg
+    import oracle
+    oracle.build()
+    mesh = mg.wall_box(**SAMPLE)
+    M = oracle.Mesh(mesh)
+    S = oracle.Solver(M, oracle.params(**PARAMS))
+    W, G = mg.uniform_state(M.nc, mach=PARAMS["mach"])
+    S.set_state(W, G)
+    S.run(args.warmup, multigrid=True)
+    t0 = time.perf_counter()
+    S.run(args.steps, multigrid=True)
+    dt = time.perf_counter() - t0
+    value = M.nc * args.steps / dt / 1e6
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = (f"each step one V-cycle of the same layout and physics at {SAMPLE['nx']}x{SAMPLE['ny']}x{SAMPLE['nz']} "
+              f"({M.nc:,} cells) instead of the full 96x64x64 box")
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                      "data": "synthetic", "config": {"workload": workload_name(SAMPLE)},
+                      "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                       "sample": sample},
+                      "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--size", default="full", choices=["full", "small"],
+                    help="small: the same layout at 48x32x32 (profiling captures only)")
+    args = ap.parse_args()
+    global WORKLOAD
+    if args.size == "small":
+        WORKLOAD = dict(nx=48, ny=32, nz=32, n_prism=18)
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    rank, world, local = dist_env()
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import meshgen as mg
+    import paper_2402_02075_gb300 as cg
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    mesh = mg.wall_box(**WORKLOAD)
+    P = cg.default_params(**PARAMS)
+    t0 = time.perf_counter()
+    ctx = cg.Context(P)
+    ctx.mesh_upload(mesh)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    levels = [ctx.level_info(l) for l in range(P.n_levels)]
+    nc = levels[0][0]
+    # Gauss points: every cell face counted from its cells (12 per tet, 18 per prism, 24 per hex),
+    # plus the non-periodic boundary faces once more, halved
+    per_cell = np.array([0, 0, 0, 0, 12, 18, 24])[mesh["cell_type"]].sum()
+    bnv = np.diff(mesh["bface_ptr"])[mesh["bface_tag"] < 100]
+    ngp = int(per_cell + bnv.sum()) // 2
+    W, G = mg.uniform_state(nc, mach=PARAMS["mach"])
+    Wd, Gd = torch.from_numpy(W).cuda(), torch.from_numpy(G).cuda()
+    ctx.state_init(Wd, Gd)
+    ctx.vcycle(args.warmup, history=False)
+    stream = ctx.stream
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.profile(True)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        ctx.vcycle(args.steps, history=False)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    k_ms, k_n = ctx.kernel_stats(0)
+    r_ms, r_n = ctx.kernel_stats(1)
+    g_ms, g_n = ctx.kernel_stats(2)
+    ctx.profile(False)
+    ms_max = max_over_ranks(ms)
+    value = world * nc * args.steps / (ms_max * 1e-3) / 1e6
+    # end to end through the public API with host buffers: per step, the state is copied in from
+    # pinned host memory (cgks_state_init) and the residual norm is read back (cgks_vcycle)
+    Wo, Go, ao = ctx.state_get()
+    Wh, Gh, ah = Wo.cpu().pin_memory(), Go.cpu().pin_memory(), ao.cpu().pin_memory()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.state_init(Wh, Gh, ah)
+        ctx.vcycle(1, history=True)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": world * nc * args.steps / e2e_s / 1e6, "unit": UNIT,
+           "h2d_bytes_per_step": int(Wh.numel() + Gh.numel() + ah.numel()) * 8, "d2h_bytes_per_step": 8}
+    peak = cg.cgks_fp64_peak()
+    k_avg = k_ms / max(k_n, 1)
+    roofline = {"bound": "alu", "kernel": "k_gks_points (FP64 gas-kinetic flux per Gauss point)",
+                "achieved": None, "peak": peak, "unit": "TFLOP/s", "frac": None,
+                "peak_source": "measured FP64 FMA-chain rate of this GPU (cgks_fp64_peak)",
+                "traffic": None, "kernel_ms": k_avg, "launches": k_n,
+                "other_kernels_ms": {"k_reconstruct": r_ms / max(r_n, 1), "k_gather": g_ms / max(g_n, 1)}}
+    if FLOP_PER_GP:
+        ach = FLOP_PER_GP * ngp / (k_avg * 1e-3) / 1e12
+        roofline.update(achieved=ach, frac=ach / peak, flop_per_gauss_point=FLOP_PER_GP)
+    if DRAM_BYTES_PER_GP:
+        roofline["traffic"] = DRAM_BYTES_PER_GP * ngp
+    launches = launches_per_vcycle({f: getattr(P, f) for f in ("dt_mode", "pre", "post", "n_levels", "coarse_steps")})
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded mesh, free-stream start)",
+           "config": {"workload": workload_name(WORKLOAD), "cells_per_level": [l[0] for l in levels],
+                      "faces_per_level": [l[1] for l in levels], "gauss_points": ngp,
+                      "parallelism": "replicas" if world > 1 else "single GPU",
+                      "l2": "working set (~6 GB) far above L2 (129 MB); no flush needed",
+                      "setup_s": setup_s, "params": {k: v for k, v in PARAMS.items()}},
+           "e2e": e2e, "gpu_launches": launches * args.steps, "roofline": roofline, "clocks": clk.summary()}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline()
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -160,6 +160,14 @@ cgks_status cgks_adjoint(cgks_ctx* ctx, const double* wall_disp_modes, int n_mod
  * from a register-resident FMA chain kernel; the roofline denominator of the FP64-bound kernels. */
 cgks_status cgks_fp64_peak(double* tflops);
 
+/* Kernel timing for roofline measurement.  cgks_profile(ctx, 1) records CUDA events on the
+ * context stream around every launch of the three fine-level kernels (0: Gauss-point gas-kinetic
+ * flux, 1: reconstruction, 2: gather/update) until cgks_profile(ctx, 0).  cgks_kernel_stats
+ * synchronises the stream and returns (host outputs) the summed device time in milliseconds and
+ * the number of launches of kernel `which` recorded since profiling was enabled. */
+cgks_status cgks_profile(cgks_ctx* ctx, int enable);
+cgks_status cgks_kernel_stats(cgks_ctx* ctx, int which, double* ms, int64_t* launches);
+
 /* Text of the last error of ctx (or of the last failed cgks_create when ctx is NULL). */
 const char* cgks_last_error(const cgks_ctx* ctx);
 

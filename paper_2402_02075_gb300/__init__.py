@@ -24,7 +24,7 @@ STATUS = {0: "CGKS_OK", 1: "CGKS_EINVAL", 2: "CGKS_ENOMEM", 3: "CGKS_ECUDA", 4: 
 EXPORTS = ["cgks_default_params", "cgks_create", "cgks_destroy", "cgks_set_params", "cgks_mesh_upload",
            "cgks_level_info", "cgks_coarse_map", "cgks_level_geometry", "cgks_fine_moments", "cgks_state_init",
            "cgks_state_get", "cgks_residual", "cgks_kfvs_residual", "cgks_step", "cgks_vcycle", "cgks_steady_solve",
-           "cgks_adjoint", "cgks_fp64_peak", "cgks_last_error"]
+           "cgks_adjoint", "cgks_fp64_peak", "cgks_profile", "cgks_kernel_stats", "cgks_last_error"]
 
 
 class CgksError(RuntimeError):
@@ -70,6 +70,8 @@ def load(path: str = LIB_PATH):
                                   C.POINTER(C.c_double)],
             "cgks_adjoint": [P, d, C.c_int, d, d],
             "cgks_fp64_peak": [C.POINTER(C.c_double)],
+            "cgks_profile": [P, C.c_int],
+            "cgks_kernel_stats": [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)],
             "cgks_last_error": [P],
         }
         for name, args in sig.items():
@@ -185,8 +187,9 @@ class Context:
         return m2
 
     def state_init(self, W, G=None, alpha=None):
+        """W, G, alpha: float64 contiguous tensors on the GPU or in pinned host memory."""
         for x in (W, G, alpha):
-            assert x is None or (x.is_cuda and x.dtype == self.torch.float64 and x.is_contiguous())
+            assert x is None or ((x.is_cuda or x.is_pinned()) and x.dtype == self.torch.float64 and x.is_contiguous())
         _check(load().cgks_state_init(self.h, _ptr(W), _ptr(G), _ptr(alpha)), self.h)
 
     def state_get(self):
@@ -216,6 +219,16 @@ class Context:
         h = np.zeros(max(n, 1))
         _check(load().cgks_vcycle(self.h, n, h.ctypes.data_as(C.POINTER(C.c_double)) if history else None), self.h)
         return h[:n]
+
+    def profile(self, enable=True):
+        _check(load().cgks_profile(self.h, int(bool(enable))), self.h)
+
+    def kernel_stats(self, which):
+        """(total device ms, launches) of fine kernel `which` (0 Gauss-point flux, 1 reconstruction,
+        2 gather) since profiling was enabled."""
+        ms, n = C.c_double(), C.c_int64()
+        _check(load().cgks_kernel_stats(self.h, which, C.byref(ms), C.byref(n)), self.h)
+        return ms.value, n.value
 
     def steady_solve(self, multigrid=True, drop=1e-10, max_iters=100000, raise_on_notconv=True):
         it, fd, sec = C.c_int64(), C.c_double(), C.c_double()

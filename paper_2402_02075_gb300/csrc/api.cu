@@ -159,9 +159,67 @@ cgks_status scan_exclusive(cgks_ctx* ctx, const int32_t* in, int32_t* out, int64
   return CGKS_OK;
 }
 
+// ---- kernel timing ---------------------------------------------------------------------------
+
+static cudaEvent_t take_event(cgks_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+ProfScope::ProfScope(cgks_ctx* ctx, int kind) : c(ctx), k(kind) {
+  if (!c->prof) return;
+  cudaEvent_t e0 = take_event(c);
+  e1 = take_event(c);
+  cudaEventRecord(e0, c->stream);
+  c->prof_ev[k].push_back({e0, e1});
+}
+
+ProfScope::~ProfScope() {
+  if (e1) cudaEventRecord(e1, c->stream);
+}
+
+static void release_events(cgks_ctx* c) {
+  for (auto& v : c->prof_ev) {
+    for (auto& p : v) {
+      c->ev_pool.push_back(p.first);
+      c->ev_pool.push_back(p.second);
+    }
+    v.clear();
+  }
+}
+
 // ---- C ABI --------------------------------------------------------------------------------------
 
 extern "C" {
+
+cgks_status cgks_profile(cgks_ctx* ctx, int enable) {
+  if (!ctx) return CGKS_EINVAL;
+  CK(cudaStreamSynchronize(ctx->stream));
+  release_events(ctx);
+  ctx->prof = enable != 0;
+  return CGKS_OK;
+}
+
+cgks_status cgks_kernel_stats(cgks_ctx* ctx, int which, double* ms, int64_t* launches) {
+  if (!ctx) return CGKS_EINVAL;
+  if (which < 0 || which > 2) return cgks_fail(ctx, CGKS_EINVAL, "kernel id must be 0, 1 or 2");
+  CK(cudaStreamSynchronize(ctx->stream));
+  double total = 0.0;
+  for (auto& p : ctx->prof_ev[which]) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, p.first, p.second));
+    total += t;
+  }
+  if (ms) *ms = total;
+  if (launches) *launches = (int64_t)ctx->prof_ev[which].size();
+  return CGKS_OK;
+}
 
 cgks_status cgks_default_params(cgks_params* p) {
   if (!p) return CGKS_EINVAL;
@@ -232,6 +290,8 @@ cgks_status cgks_create(const cgks_params* params, void* cuda_stream, cgks_ctx**
 cgks_status cgks_destroy(cgks_ctx* ctx) {
   if (!ctx) return CGKS_OK;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  release_events(ctx);
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   free_list(ctx->mesh_allocs);
   free_list(ctx->ctx_allocs);
   if (ctx->h_err) cudaFreeHost(ctx->h_err);

@@ -55,11 +55,17 @@ cgks_status fine_fluxes(cgks_ctx* ctx, const double* W, const double* G, const d
   const Phys ph = make_phys(ctx->P);
   ReconArgs ra{F.nc, F.nf, F.ctype, F.cf, F.fL, F.fR, F.ftag, F.cside, F.fnrm, F.Kop, F.ggw, F.lsw, F.aux, F.dtw,
                F.vol, W, G, alpha, ctx->rc, ctx->dt, ph, ctx->derr};
-  k_reconstruct<<<grid_for(F.nc, 128), 128, 0, ctx->stream>>>(ra);
+  {
+    ProfScope ps(ctx, 1);
+    k_reconstruct<<<grid_for(F.nc, 128), 128, 0, ctx->stream>>>(ra);
+  }
   if (ctx->P.dt_mode == 1) CKS(global_min_dt(ctx, ctx->dt, F.nc));
   PointArgs pa{F.ngp, F.nf, F.nc, F.gp_face, F.fL, F.fR, F.ftag, F.gp_x, F.gp_A, F.fshift, F.ctr, ctx->rc,
                ctx->dt, ctx->gpF, ctx->gpW, ctx->gpa, ph, ctx->derr};
-  k_gks_points<<<grid_for(F.ngp, 128), 128, 0, ctx->stream>>>(pa);
+  {
+    ProfScope ps(ctx, 0);
+    k_gks_points<<<grid_for(F.ngp, 128), 128, 0, ctx->stream>>>(pa);
+  }
   CK(cudaGetLastError());
   return CGKS_OK;
 }
@@ -69,7 +75,10 @@ cgks_status fine_gather(cgks_ctx* ctx, const double* W_in, double* W_out, double
   const Fine& F = ctx->F;
   GatherArgs ga{F.nc, F.ngp, F.ctype, F.cside, F.cf, F.gp_ptr, F.gp_A, ctx->gpF, ctx->gpW, ctx->gpa, F.vol,
                 ctx->dt, W_in, W_out, res, G_out, alpha_out, update, ctx->P.gamma, ctx->derr};
-  k_gather<<<grid_for(F.nc, 128), 128, 0, ctx->stream>>>(ga);
+  {
+    ProfScope ps(ctx, 2);
+    k_gather<<<grid_for(F.nc, 128), 128, 0, ctx->stream>>>(ga);
+  }
   CK(cudaGetLastError());
   return CGKS_OK;
 }

@@ -99,6 +99,19 @@ struct cgks_ctx {
   int64_t iters = 0;
   std::vector<void*> mesh_allocs;   // freed on re-upload / destroy
   std::vector<void*> ctx_allocs;    // freed on destroy
+  // kernel timing (cgks_profile): event pairs per fine kernel kind
+  bool prof = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[3];
+  std::vector<cudaEvent_t> ev_pool;
+};
+
+// event pair recorded around one launch of fine kernel kind k when profiling is enabled
+struct ProfScope {
+  cgks_ctx* c;
+  int k;
+  cudaEvent_t e1 = nullptr;
+  ProfScope(cgks_ctx* ctx, int kind);
+  ~ProfScope();
 };
 
 // ---- error helpers (host) ---------------------------------------------------------------------
