@@ -168,6 +168,22 @@ cgks_status cgks_fp64_peak(double* tflops);
 cgks_status cgks_profile(cgks_ctx* ctx, int enable);
 cgks_status cgks_kernel_stats(cgks_ctx* ctx, int which, double* ms, int64_t* launches);
 
+/* Density-residual norm sqrt(mean_i (res_rho[i] / vol[i])^2) (the quantity cgks_residual reports)
+ * for callers that cannot let the library allocate device memory: applications that hand each
+ * component a fixed, accounted slice of GPU memory from their own pool, and loops that cannot absorb
+ * the device-wide synchronisation an allocation or free may cause.  The paper has no counterpart.
+ *   res_rho, vol  device double[n] (the density row of a residual and the cell volumes)
+ *   norm          device double, written on `cuda_stream` (cudaStream_t; NULL = legacy stream)
+ * Nothing is allocated: the partial sums live in a 512 KiB array inside the loaded module, so
+ * n may be at most 67,108,864 (65,536 tiles of 1,024 cells); larger n returns CGKS_EINVAL.  The
+ * first call on each device looks up that array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  All calls share the array: calls whose GPU work
+ * overlaps (other streams, other host threads) race and may return wrong norms; serialise them.
+ * Each call overwrites the partial sums it uses, so no clearing is needed between calls.  No
+ * context is involved: on failure cgks_last_error(NULL) gives the message. */
+cgks_status cgks_density_norm_noalloc(const double* res_rho, const double* vol, int64_t n, void* cuda_stream,
+                                      double* norm);
+
 /* Text of the last error of ctx (or of the last failed cgks_create when ctx is NULL). */
 const char* cgks_last_error(const cgks_ctx* ctx);
 

@@ -24,7 +24,8 @@ STATUS = {0: "CGKS_OK", 1: "CGKS_EINVAL", 2: "CGKS_ENOMEM", 3: "CGKS_ECUDA", 4: 
 EXPORTS = ["cgks_default_params", "cgks_create", "cgks_destroy", "cgks_set_params", "cgks_mesh_upload",
            "cgks_level_info", "cgks_coarse_map", "cgks_level_geometry", "cgks_fine_moments", "cgks_state_init",
            "cgks_state_get", "cgks_residual", "cgks_kfvs_residual", "cgks_step", "cgks_vcycle", "cgks_steady_solve",
-           "cgks_adjoint", "cgks_fp64_peak", "cgks_profile", "cgks_kernel_stats", "cgks_last_error"]
+           "cgks_adjoint", "cgks_fp64_peak", "cgks_profile", "cgks_kernel_stats", "cgks_density_norm_noalloc",
+           "cgks_last_error"]
 
 
 class CgksError(RuntimeError):
@@ -72,6 +73,7 @@ def load(path: str = LIB_PATH):
             "cgks_fp64_peak": [C.POINTER(C.c_double)],
             "cgks_profile": [P, C.c_int],
             "cgks_kernel_stats": [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)],
+            "cgks_density_norm_noalloc": [d, d, C.c_int64, P, d],
             "cgks_last_error": [P],
         }
         for name, args in sig.items():
