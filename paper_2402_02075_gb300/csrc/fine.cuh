@@ -8,12 +8,23 @@
 //                      alpha_{p,k} (Sec. 3.3)
 //   gather_body      : per cell, fixed-order sums of the Gauss-point records -> residual,
 //                      Gauss-Green gradient times the compression factor, optional explicit update
-// The FP64 pipe bounds this path: micro-slopes use the closed-form solution of the 5x5 moment
-// system, moment matrices are applied to combined slopes, and full-space moments of time
-// derivatives come from Euler-flux Jacobians (the derivative of an equilibrium moment along a slope).
+// The FP64 pipe bounds this path (FP64 runs at 1/62 of the FP32 rate on this GPU), so the code is
+// written for few FP64 instructions: one reciprocal and one square-root family per Maxwellian,
+// micro-slopes from the closed-form solution of the 5x5 moment system, the half-space erfc/exp
+// seeds computed once per side, moment matrices applied to the slopes, and full-space moments of
+// time derivatives from Euler-flux Jacobian products (the derivative of an equilibrium moment along
+// a slope direction).
 #pragma once
 #include "internal.cuh"
 #include "kinetic.cuh"
+
+HD double rsqrt_hd(double x) {
+#ifdef __CUDA_ARCH__
+  return rsqrt(x);
+#else
+  return 1.0 / sqrt(x);
+#endif
+}
 
 struct ReconArgs {
   int64_t nc, nf;
@@ -111,10 +122,14 @@ HD void reconstruct_body(int64_t i, const ReconArgs& a) {
     const double rden = 1.0 / (Q0[q] * Q0[q] + beta1 + 1e-40);
     const double bt1 = beta1 * rden, bt2 = beta2 * rden;
     const double sig = fabs(bt2 - bt1);
-    const double r1 = sig / (ph.weno_eps + bt1), r2 = sig / (ph.weno_eps + bt2);
-    const double w1 = g1 * (1.0 + r1 * r1), w2 = g2 * (1.0 + r2 * r2);
-    const double ws = 1.0 / (w1 + w2);
-    const double c2 = (w2 * ws) / g2, c1 = w1 * ws - (w2 * ws) * (g1 / g2);
+    // w_m = g_m (1 + (sig/d_m)^2) with d_m = eps + beta~_m, normalised with one division:
+    // w_1 : w_2 = g_1 (d_1^2 + sig^2) d_2^2 : g_2 (d_2^2 + sig^2) d_1^2
+    const double d1 = ph.weno_eps + bt1, d2 = ph.weno_eps + bt2;
+    const double s2 = sig * sig, d11 = d1 * d1, d22 = d2 * d2;
+    const double A1 = g1 * (d11 + s2) * d22, A2 = g2 * (d22 + s2) * d11;
+    const double inv = 1.0 / (A1 + A2);
+    const double w1 = A1 * inv, w2 = A2 * inv;
+    const double c2 = w2 * (1.0 / g2), c1 = w1 - w2 * (g1 / g2);
     out[10 * q + 0] = c2 * a0 + c1 * Q0[q];
 #pragma unroll
     for (int d = 0; d < 3; ++d) out[10 * q + 1 + d] = c2 * bq[d] + c1 * p1[d];
@@ -129,14 +144,14 @@ HD void reconstruct_body(int64_t i, const ReconArgs& a) {
   const double u[3] = {Q0[1] * r, Q0[2] * r, Q0[3] * r};
   const double p = (ph.gamma - 1.0) * (Q0[4] - 0.5 * Q0[0] * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
   const double c = sqrt(ph.gamma * p * r);
-  const double nu = ph.viscous ? ph.mu * r : 0.0;
   const double V = a.vol[i];
+  const double nu2 = ph.viscous ? 2.0 * ph.mu * r / V : 0.0;
   double s = 0.0;
   for (int m = 0; m < nt; ++m) {
     const double S = a.dtw[(4 * m + 3) * nc + i];
     const double un = fabs(u[0] * a.dtw[(4 * m) * nc + i] + u[1] * a.dtw[(4 * m + 1) * nc + i] +
                            u[2] * a.dtw[(4 * m + 2) * nc + i]);
-    s += un + S * c + 2.0 * nu * S * S / V;
+    s += un + S * c + nu2 * S * S;
   }
   a.dt[i] = ph.cfl_fine * V / s;
   if (!(Q0[0] > 0.0) || !(p > 0.0) || !isfinite(Q0[4])) set_err(a.err, CGKS_ENAN, (int)i, 2);
@@ -144,76 +159,54 @@ HD void reconstruct_body(int64_t i, const ReconArgs& a) {
 
 // ---- gas-kinetic point flux -------------------------------------------------------------------
 
-struct Mom {
-  double m[7];        // u-moments (half or full space) times rho
-  double v[6], w[6];  // tangential moments <v^k>, <w^k>
-  double x2, x4;      // <xi^2>, <xi^4>
+// a Maxwellian in the face frame with the reciprocals the moments and slopes need
+struct Maxw {
+  double rho, U, V, W;  // density, velocity (normal, tangential 1, tangential 2)
+  double r, p, h;       // 1/rho, pressure, h = p/rho = 1/(2 lambda)
+  double l2, q2;        // 2 lambda = 1/h, |U|^2 + (K+3) h
 };
 
-HD void tang_moments(double V, double h, double* v) {
-  v[0] = 1.0;
-  v[1] = V;
-#pragma unroll
-  for (int n = 0; n + 2 < 6; ++n) v[n + 2] = V * v[n + 1] + (n + 1) * h * v[n];
+HD bool make_maxw(const double w[5], double gm1, double K, Maxw& g) {
+  g.rho = w[0];
+  g.r = 1.0 / w[0];
+  g.U = w[1] * g.r;
+  g.V = w[2] * g.r;
+  g.W = w[3] * g.r;
+  g.p = gm1 * (w[4] - 0.5 * (w[1] * g.U + w[2] * g.V + w[3] * g.W));
+  g.h = g.p * g.r;
+  g.l2 = 1.0 / g.h;
+  g.q2 = g.U * g.U + g.V * g.V + g.W * g.W + (K + 3.0) * g.h;
+  return w[0] > 0.0 && g.p > 0.0;
 }
 
-HD void make_mom(const Prim<double>& g, int side, double K, Mom& M) {
-  u_moments<double, 6>(g.U, g.lam, side, M.m);
-#pragma unroll
-  for (int k = 0; k < 7; ++k) M.m[k] *= g.rho;
-  const double h = 0.5 / g.lam;
-  tang_moments(g.V, h, M.v);
-  tang_moments(g.W, h, M.w);
-  M.x2 = K * h;
-  M.x4 = K * (K + 2.0) * h * h;
+// <u^0>, <u^1> over u > 0 (side +1) or u < 0 (side -1), normalised by rho:
+// 1/2 erfc(-s sqrt(lambda) U) and U <u^0> + s exp(-lambda U^2) / (2 sqrt(pi lambda))
+HD void half_seeds(const Maxw& g, double side, double& m0, double& m1) {
+  const double lam = 0.5 * g.l2;
+  const double isl = rsqrt_hd(lam);
+  const double sl = lam * isl;
+  m0 = 0.5 * erfc(-side * sl * g.U);
+  m1 = g.U * m0 + side * (0.5 * 0.56418958354775628695) * exp(-lam * g.U * g.U) * isl;
 }
 
-// out = <u^KU v^KV w^KW (s . psi) psi>, psi = (1, u, v, w, (u^2 + v^2 + w^2 + xi^2)/2)
-template <int KU, int KV, int KW>
-HD void psi_apply(const Mom& M, const double s[5], double out[5]) {
-  const double* m = M.m;
-  const double* v = M.v;
-  const double* w = M.w;
-#define MM(a, b, c) (m[KU + (a)] * (v[KV + (b)] * w[KW + (c)]))
-  const double e00 = MM(0, 0, 0), e01 = MM(1, 0, 0), e11 = MM(2, 0, 0);
-  const double e02 = MM(0, 1, 0), e12 = MM(1, 1, 0), e22 = MM(0, 2, 0);
-  const double e03 = MM(0, 0, 1), e13 = MM(1, 0, 1), e23 = MM(0, 1, 1), e33 = MM(0, 0, 2);
-  const double e04 = 0.5 * (e11 + e22 + e33 + M.x2 * e00);
-  const double e14 = 0.5 * (MM(3, 0, 0) + MM(1, 2, 0) + MM(1, 0, 2) + M.x2 * e01);
-  const double e24 = 0.5 * (MM(2, 1, 0) + MM(0, 3, 0) + MM(0, 1, 2) + M.x2 * e02);
-  const double e34 = 0.5 * (MM(2, 0, 1) + MM(0, 2, 1) + MM(0, 0, 3) + M.x2 * e03);
-  const double e44 = 0.25 * (MM(4, 0, 0) + MM(0, 4, 0) + MM(0, 0, 4) + M.x4 * e00 +
-                             2.0 * (MM(2, 2, 0) + MM(2, 0, 2) + MM(0, 2, 2)) + 2.0 * M.x2 * (e11 + e22 + e33));
-#undef MM
-  out[0] = e00 * s[0] + e01 * s[1] + e02 * s[2] + e03 * s[3] + e04 * s[4];
-  out[1] = e01 * s[0] + e11 * s[1] + e12 * s[2] + e13 * s[3] + e14 * s[4];
-  out[2] = e02 * s[0] + e12 * s[1] + e22 * s[2] + e23 * s[3] + e24 * s[4];
-  out[3] = e03 * s[0] + e13 * s[1] + e23 * s[2] + e33 * s[3] + e34 * s[4];
-  out[4] = e04 * s[0] + e14 * s[1] + e24 * s[2] + e34 * s[3] + e44 * s[4];
-}
-
-// micro-slope s with <s psi> = dW under the full Maxwellian g (closed form of the 5x5 system)
-HD void slope_solve(const Prim<double>& g, double K, const double dW[5], double s[5]) {
-  const double r = 1.0 / g.rho;
-  const double d0 = dW[0] * r, d1 = dW[1] * r, d2 = dW[2] * r, d3 = dW[3] * r, d4 = dW[4] * r;
-  const double q2 = g.U * g.U + g.V * g.V + g.W * g.W + (K + 3.0) * 0.5 / g.lam;
-  const double R4 = 2.0 * d4 - q2 * d0;
+// micro-slope s with <s psi> = dW under the full Maxwellian g (closed form of the 5x5 system);
+// ck = 4 lambda^2 / (K + 3)
+HD void slope_solve(const Maxw& g, double ck, const double dW[5], double s[5]) {
+  const double d0 = dW[0] * g.r, d1 = dW[1] * g.r, d2 = dW[2] * g.r, d3 = dW[3] * g.r, d4 = dW[4] * g.r;
+  const double R4 = 2.0 * d4 - g.q2 * d0;
   const double R1 = d1 - g.U * d0, R2 = d2 - g.V * d0, R3 = d3 - g.W * d0;
-  const double l2 = 2.0 * g.lam;
-  s[4] = (l2 * l2 / (K + 3.0)) * (R4 - 2.0 * (g.U * R1 + g.V * R2 + g.W * R3));
-  s[1] = l2 * R1 - g.U * s[4];
-  s[2] = l2 * R2 - g.V * s[4];
-  s[3] = l2 * R3 - g.W * s[4];
-  s[0] = d0 - g.U * s[1] - g.V * s[2] - g.W * s[3] - 0.5 * s[4] * q2;
+  s[4] = ck * (R4 - 2.0 * (g.U * R1 + g.V * R2 + g.W * R3));
+  s[1] = g.l2 * R1 - g.U * s[4];
+  s[2] = g.l2 * R2 - g.V * s[4];
+  s[3] = g.l2 * R3 - g.W * s[4];
+  s[0] = d0 - g.U * s[1] - g.V * s[2] - g.W * s[3] - 0.5 * s[4] * g.q2;
 }
 
 // directional derivative of the Euler flux through the k-th axis of the face frame along dW:
 // equals <u_k (a . psi) psi> under the full Maxwellian when <a psi> = dW
-HD void euler_jvp(const double w[5], const Prim<double>& g, double gm1, int k, const double dW[5], double out[5]) {
-  const double r = 1.0 / w[0];
+HD void euler_jvp(const double w[5], const Maxw& g, double gm1, int k, const double dW[5], double out[5]) {
   const double u[3] = {g.U, g.V, g.W};
-  const double du[3] = {(dW[1] - u[0] * dW[0]) * r, (dW[2] - u[1] * dW[0]) * r, (dW[3] - u[2] * dW[0]) * r};
-  const double p = 0.5 * w[0] / g.lam;
+  const double du[3] = {(dW[1] - u[0] * dW[0]) * g.r, (dW[2] - u[1] * dW[0]) * g.r, (dW[3] - u[2] * dW[0]) * g.r};
   const double dp = gm1 * (dW[4] - (u[0] * dW[1] + u[1] * dW[2] + u[2] * dW[3]) +
                            0.5 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) * dW[0]);
   const double mk = w[1 + k], dmk = dW[1 + k];
@@ -221,19 +214,20 @@ HD void euler_jvp(const double w[5], const Prim<double>& g, double gm1, int k, c
 #pragma unroll
   for (int j = 0; j < 3; ++j) out[1 + j] = dmk * u[j] + mk * du[j];
   out[1 + k] += dp;
-  out[4] = du[k] * (w[4] + p) + u[k] * (dW[4] + dp);
+  out[4] = du[k] * (w[4] + g.p) + u[k] * (dW[4] + dp);
 }
 
 // gradient (global frame) of a reconstruction polynomial at offset X from its centroid
 HD void eval_gradient(const double* rcp, const double X[3], double Gq[15]) {
+  const double X2[3] = {2.0 * X[0], 2.0 * X[1], 2.0 * X[2]};
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
     const double2* c2 = reinterpret_cast<const double2*>(rcp + 10 * q);
     const double2 A = c2[0], B = c2[1], C = c2[2], D = c2[3], E = c2[4];
     // (r0 r1) (r2 r3) (r4 r5) (r6 r7) (r8 r9): 1 X Y Z X^2 Y^2 Z^2 XY YZ XZ
-    Gq[3 * q + 0] = A.y + 2.0 * C.x * X[0] + D.y * X[1] + E.y * X[2];
-    Gq[3 * q + 1] = B.x + 2.0 * C.y * X[1] + D.y * X[0] + E.x * X[2];
-    Gq[3 * q + 2] = B.y + 2.0 * D.x * X[2] + E.x * X[1] + E.y * X[0];
+    Gq[3 * q + 0] = A.y + C.x * X2[0] + D.y * X[1] + E.y * X[2];
+    Gq[3 * q + 1] = B.x + C.y * X2[1] + D.y * X[0] + E.x * X[2];
+    Gq[3 * q + 2] = B.y + D.x * X2[2] + E.x * X[1] + E.y * X[0];
   }
 }
 
@@ -262,65 +256,150 @@ HD void rotate_gradient(const double Gq[15], const double* e[3], double D[3][5])
   }
 }
 
+// ---- moments in the frame moving with the tangential velocity --------------------------------
+// With c = v - V, d = w - W (full-space Gaussians of variance h), psi = T psi' where
+// psi' = (1, u, c, d, (u^2 + c^2 + d^2 + xi^2)/2) and T adds V, W, (V^2 + W^2)/2 terms.  Odd moments of
+// c and d vanish, so the matrices <u^k psi' psi'^T>, <u^k c psi' psi'^T>, <u^k d psi' psi'^T> are sparse;
+// a slope s becomes s' = T^T s and a moment vector o' becomes T o'.
+struct MomP {
+  double M[7];            // rho <u^k>, k = 0..6 (half or full space)
+  double h, sig, tau4;    // h = p/rho, sig = h + <xi^2>/2, tau4 = 2 h^2 + h <xi^2> + <xi^4>/4
+  double hs;              // h (2 h + <xi^2>/2)
+  double V, W, E;         // tangential velocity and (V^2 + W^2)/2
+};
+
+HD void make_momp(const Maxw& g, double m0, double m1, double K, MomP& P) {
+  double m[7];
+  m[0] = m0;
+  m[1] = m1;
+#pragma unroll
+  for (int n = 0; n + 2 < 7; ++n) m[n + 2] = g.U * m[n + 1] + (n + 1) * g.h * m[n];
+#pragma unroll
+  for (int k = 0; k < 7; ++k) P.M[k] = g.rho * m[k];
+  const double h = g.h, x2 = K * h, x4 = K * (K + 2.0) * h * h;
+  P.h = h;
+  P.sig = h + 0.5 * x2;
+  P.tau4 = 2.0 * h * h + h * x2 + 0.25 * x4;
+  P.hs = h * (2.0 * h + 0.5 * x2);
+  P.V = g.V;
+  P.W = g.W;
+  P.E = 0.5 * (g.V * g.V + g.W * g.W);
+}
+
+// s' = T^T s
+HD void to_primed(const MomP& P, const double s[5], double sp[5]) {
+  sp[0] = s[0] + P.V * s[2] + P.W * s[3] + P.E * s[4];
+  sp[1] = s[1];
+  sp[2] = s[2] + P.V * s[4];
+  sp[3] = s[3] + P.W * s[4];
+  sp[4] = s[4];
+}
+
+// out += c T o'
+HD void add_from_primed(const MomP& P, const double o[5], double c, double out[5]) {
+  out[0] += c * o[0];
+  out[1] += c * o[1];
+  out[2] += c * (P.V * o[0] + o[2]);
+  out[3] += c * (P.W * o[0] + o[3]);
+  out[4] += c * (P.E * o[0] + P.V * o[2] + P.W * o[3] + o[4]);
+}
+
+// o' = <u^k (s' . psi') psi'>
+template <int k>
+HD void papp(const MomP& P, const double s[5], double o[5]) {
+  const double* M = P.M;
+  const double Pk = 0.5 * M[k + 2] + P.sig * M[k];
+  const double Qk = 0.5 * M[k + 3] + P.sig * M[k + 1];
+  const double Rk = 0.25 * M[k + 4] + P.sig * M[k + 2] + P.tau4 * M[k];
+  const double hM = P.h * M[k];
+  o[0] = M[k] * s[0] + M[k + 1] * s[1] + Pk * s[4];
+  o[1] = M[k + 1] * s[0] + M[k + 2] * s[1] + Qk * s[4];
+  o[2] = hM * s[2];
+  o[3] = hM * s[3];
+  o[4] = Pk * s[0] + Qk * s[1] + Rk * s[4];
+}
+
+// o' += <u^k c (s' . psi') psi'> (J = 2) or <u^k d (s' . psi') psi'> (J = 3)
+template <int k, int J>
+HD void papp_t_add(const MomP& P, const double s[5], double o[5]) {
+  const double* M = P.M;
+  const double hM0 = P.h * M[k], hM1 = P.h * M[k + 1];
+  const double S4 = 0.5 * P.h * M[k + 2] + P.hs * M[k];
+  o[0] += hM0 * s[J];
+  o[1] += hM1 * s[J];
+  o[J] += hM0 * s[0] + hM1 * s[1] + S4 * s[4];
+  o[4] += S4 * s[J];
+}
+
+// o' = <u^k (a . u) psi'> with the three slopes in primed form: u a_n + v a_t1 + w a_t2,
+// v = V + c, w = W + d
+template <int k>
+HD void papp_au(const MomP& P, const double an[5], const double a1[5], const double a2[5], double o[5]) {
+  double comb[5], t[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) comb[q] = P.V * a1[q] + P.W * a2[q];
+  papp<k + 1>(P, an, o);
+  papp<k>(P, comb, t);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) o[q] += t[q];
+  papp_t_add<k, 2>(P, a1, o);
+  papp_t_add<k, 3>(P, a2, o);
+}
+
 // one side of the interface: micro-slopes of the initial distribution, its contribution to the
 // equilibrium slopes, the time-integrated flux, the state at dt and the time-integrated state
-template <int SIDE>
-HD void side_terms(const double D[3][5], const double w[5], const Prim<double>& g, double K, double gm1, double tau,
-                   double q4, double q5, double edt, double dtf, double dWc[3][5], double Facc[5], double Wacc[5],
-                   double Iacc[5]) {
+HD void side_terms(const double D[3][5], const double w[5], const Maxw& g, double m0, double m1, double K, double ck,
+                   double gm1, double tau, double q4, double q5, double edt, double dtf, double dWc[3][5],
+                   double Facc[5], double Wacc[5], double Iacc[5]) {
+  MomP P;
+  make_momp(g, m0, m1, K, P);
   double a[3][5];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) slope_solve(g, K, D[k], a[k]);
+  for (int k = 0; k < 3; ++k) {
+    double s[5];
+    slope_solve(g, ck, D[k], s);
+    to_primed(P, s, a[k]);
+  }
   // time slope A from <A + a.u> = 0 under the full Maxwellian: <(a.u) psi> = sum_k J_k dW_k
-  double au[5] = {0, 0, 0, 0, 0};
+  double Ap[5];
+  {
+    double t0[5], t1[5], t2[5], au[5], A[5];
+    euler_jvp(w, g, gm1, 0, D[0], t0);
+    euler_jvp(w, g, gm1, 1, D[1], t1);
+    euler_jvp(w, g, gm1, 2, D[2], t2);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) au[q] = -(t0[q] + t1[q] + t2[q]);
+    slope_solve(g, ck, au, A);
+    to_primed(P, A, Ap);
+  }
+  // half-space moments: equilibrium-slope contributions <a_k psi>
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     double t[5];
-    euler_jvp(w, g, gm1, k, D[k], t);
-#pragma unroll
-    for (int q = 0; q < 5; ++q) au[q] -= t[q];
+    papp<0>(P, a[k], t);
+    add_from_primed(P, t, 1.0, dWc[k]);
   }
-  double A[5];
-  slope_solve(g, K, au, A);
-  Mom M;
-  make_mom(g, SIDE, K, M);
-  double t0[5], t1[5], t2[5];
-  psi_apply<0, 0, 0>(M, a[0], t0);
-  psi_apply<0, 0, 0>(M, a[1], t1);
-  psi_apply<0, 0, 0>(M, a[2], t2);
-#pragma unroll
-  for (int q = 0; q < 5; ++q) {
-    dWc[0][q] += t0[q];
-    dWc[1][q] += t1[q];
-    dWc[2][q] += t2[q];
-  }
-  const double one[5] = {1.0, 0.0, 0.0, 0.0, 0.0};
-  double Va[5], VA[5], V0[5], Fa[5], FA[5], F0[5];
-  {
-    double x[5], y[5], z[5];
-    psi_apply<1, 0, 0>(M, a[0], x);
-    psi_apply<0, 1, 0>(M, a[1], y);
-    psi_apply<0, 0, 1>(M, a[2], z);
-#pragma unroll
-    for (int q = 0; q < 5; ++q) Va[q] = x[q] + y[q] + z[q];
-    psi_apply<2, 0, 0>(M, a[0], x);
-    psi_apply<1, 1, 0>(M, a[1], y);
-    psi_apply<1, 0, 1>(M, a[2], z);
-#pragma unroll
-    for (int q = 0; q < 5; ++q) Fa[q] = x[q] + y[q] + z[q];
-  }
-  psi_apply<0, 0, 0>(M, A, VA);
-  psi_apply<0, 0, 0>(M, one, V0);
-  psi_apply<1, 0, 0>(M, A, FA);
-  psi_apply<1, 0, 0>(M, one, F0);
+  // <(a.u) psi>, <u (a.u) psi>, <A psi>, <u A psi>, <psi>, <u psi>
+  double Va[5], Fa[5], VA[5], FA[5];
+  papp_au<0>(P, a[0], a[1], a[2], Va);
+  papp_au<1>(P, a[0], a[1], a[2], Fa);
+  papp<0>(P, Ap, VA);
+  papp<1>(P, Ap, FA);
+  const double* M = P.M;
+  const double V0[5] = {M[0], M[1], 0.0, 0.0, 0.5 * M[2] + P.sig * M[0]};
+  const double F0[5] = {M[1], M[2], 0.0, 0.0, 0.5 * M[3] + P.sig * M[1]};
   const double tq4 = tau * q4;
   const double etd = edt * (tau + dtf), etau = edt * tau;
+  double f[5], s[5], i[5];
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
-    Facc[q] += q4 * F0[q] - q5 * Fa[q] - tq4 * FA[q];
-    Wacc[q] += edt * V0[q] - etd * Va[q] - etau * VA[q];
-    Iacc[q] += q4 * V0[q] - q5 * Va[q] - tq4 * VA[q];
+    f[q] = q4 * F0[q] - q5 * Fa[q] - tq4 * FA[q];
+    s[q] = edt * V0[q] - etd * Va[q] - etau * VA[q];
+    i[q] = q4 * V0[q] - q5 * Va[q] - tq4 * VA[q];
   }
+  add_from_primed(P, f, 1.0, Facc);
+  add_from_primed(P, s, 1.0, Wacc);
+  add_from_primed(P, i, 1.0, Iacc);
 }
 
 struct PointArgs {
@@ -339,12 +418,12 @@ HD void gks_point_body(int64_t g, const PointArgs& a) {
   const int64_t L = a.fL[f], R = a.fR[f];
   const double x[3] = {a.gp_x[g], a.gp_x[ngp + g], a.gp_x[2 * ngp + g]};
   const double Av[3] = {a.gp_A[g], a.gp_A[ngp + g], a.gp_A[2 * ngp + g]};
-  const double wgt = sqrt(Av[0] * Av[0] + Av[1] * Av[1] + Av[2] * Av[2]);
-  const double n[3] = {Av[0] / wgt, Av[1] / wgt, Av[2] / wgt};
+  const double iw = rsqrt_hd(Av[0] * Av[0] + Av[1] * Av[1] + Av[2] * Av[2]);
+  const double n[3] = {Av[0] * iw, Av[1] * iw, Av[2] * iw};
   double t1[3], t2[3];
   face_frame(n, t1, t2);
   const double* e[3] = {n, t1, t2};
-  const double K = ph.K, gm1 = ph.gamma - 1.0;
+  const double K = ph.K, gm1 = ph.gamma - 1.0, iK3 = 1.0 / (K + 3.0);
   const bool bnd = R < 0;
   // left and right states and gradients at the point (global frame)
   const double* rcL = a.rc + (int64_t)CGKS_RC * L;
@@ -367,34 +446,35 @@ HD void gks_point_body(int64_t g, const PointArgs& a) {
   double wl[5], wr[5];
   rotate_in(WLg, n, t1, t2, wl);
   rotate_in(WRg, n, t1, t2, wr);
-  Prim<double> gl, gr;
-  const bool okl = prim_local(wl, gm1, gl), okr = prim_local(wr, gm1, gr);
+  Maxw gl, gr;
+  const bool okl = make_maxw(wl, gm1, K, gl), okr = make_maxw(wr, gm1, K, gr);
   if (!(okl && okr)) set_err(a.err, CGKS_ENAN, (int)f, 4);
-  // interface equilibrium W^c = int_{u>0} psi g^l + int_{u<0} psi g^r (Eq. compatibility2)
+  // half-space seeds of both sides, and the interface equilibrium
+  // W^c = int_{u>0} psi g^l + int_{u<0} psi g^r (Eq. compatibility2)
+  double ml0, ml1, mr0, mr1;
+  half_seeds(gl, 1.0, ml0, ml1);
+  half_seeds(gr, -1.0, mr0, mr1);
   double wc[5];
   {
-    double ml[3], mr[3];
-    u_moments<double, 2>(gl.U, gl.lam, 1, ml);
-    u_moments<double, 2>(gr.U, gr.lam, -1, mr);
-    const double ql = gl.V * gl.V + gl.W * gl.W + (K + 2.0) * 0.5 / gl.lam;
-    const double qr = gr.V * gr.V + gr.W * gr.W + (K + 2.0) * 0.5 / gr.lam;
-    wc[0] = gl.rho * ml[0] + gr.rho * mr[0];
-    wc[1] = gl.rho * ml[1] + gr.rho * mr[1];
-    wc[2] = gl.rho * gl.V * ml[0] + gr.rho * gr.V * mr[0];
-    wc[3] = gl.rho * gl.W * ml[0] + gr.rho * gr.W * mr[0];
-    wc[4] = 0.5 * (gl.rho * (ml[2] + ml[0] * ql) + gr.rho * (mr[2] + mr[0] * qr));
+    const double ml2 = gl.U * ml1 + gl.h * ml0, mr2 = gr.U * mr1 + gr.h * mr0;
+    const double ql = gl.V * gl.V + gl.W * gl.W + (K + 2.0) * gl.h;
+    const double qr = gr.V * gr.V + gr.W * gr.W + (K + 2.0) * gr.h;
+    wc[0] = gl.rho * ml0 + gr.rho * mr0;
+    wc[1] = gl.rho * ml1 + gr.rho * mr1;
+    wc[2] = gl.rho * gl.V * ml0 + gr.rho * gr.V * mr0;
+    wc[3] = gl.rho * gl.W * ml0 + gr.rho * gr.W * mr0;
+    wc[4] = 0.5 * (gl.rho * (ml2 + ml0 * ql) + gr.rho * (mr2 + mr0 * qr));
   }
-  Prim<double> gc;
-  if (!prim_local(wc, gm1, gc)) set_err(a.err, CGKS_ENAN, (int)f, 5);
+  Maxw gc;
+  if (!make_maxw(wc, gm1, K, gc)) set_err(a.err, CGKS_ENAN, (int)f, 5);
   // collision times (Sec. 2.3)
-  const double pl = 0.5 * gl.rho / gl.lam, pr = 0.5 * gr.rho / gr.lam, pc = 0.5 * gc.rho / gc.lam;
-  const double jump = fabs((pl - pr) / (pl + pr));
+  const double jump = fabs((gl.p - gr.p) / (gl.p + gr.p));
   double tau, tn;
   if (ph.viscous) {
-    tau = ph.mu / pc;
+    tau = ph.mu * (gc.r * gc.l2);  // mu / p^c
     tn = tau + ph.c_press * jump * dtf;
   } else {
-    tn = ph.eps_inviscid * dtf + ph.c_press * jump * dtf;
+    tn = (ph.eps_inviscid + ph.c_press * jump) * dtf;
     tau = tn;
   }
   // exact integrals over [0, dt] of the time coefficients of Eq. 2nd-flux
@@ -404,13 +484,13 @@ HD void gks_point_body(int64_t g, const PointArgs& a) {
   const double q3 = 0.5 * dtf * dtf - tau * dtf + tau * tn * om;
   const double q4 = tn * om;
   const double q5 = (tau * tn + tn * tn) * om - tn * dtf * edt;
-  // compression factor of this Gauss point (interior faces only)
+  // compression factor of this Gauss point (interior faces only), 1/p = l2 / rho
   double alpha = 1.0;
   if (!bnd) {
-    const double cl = sqrt(ph.gamma * pl / gl.rho), cr = sqrt(ph.gamma * pr / gr.rho);
-    const double dp = fabs(pl - pr);
-    const double dn = gl.U / cl - gr.U / cr, d1 = gl.V / cl - gr.V / cr, d2 = gl.W / cl - gr.W / cr;
-    const double A = dp / pl + dp / pr + dn * dn + (d1 * d1 + d2 * d2);
+    const double icl = rsqrt_hd(ph.gamma * gl.h), icr = rsqrt_hd(ph.gamma * gr.h);
+    const double dp = fabs(gl.p - gr.p);
+    const double dn = gl.U * icl - gr.U * icr, d1 = gl.V * icl - gr.V * icr, d2 = gl.W * icl - gr.W * icr;
+    const double A = dp * (gl.r * gl.l2 + gr.r * gr.l2) + dn * dn + (d1 * d1 + d2 * d2);
     alpha = 1.0 / (1.0 + A * A);
   }
   double dWc[3][5], Facc[5], Wacc[5], Iacc[5];
@@ -422,43 +502,47 @@ HD void gks_point_body(int64_t g, const PointArgs& a) {
   {
     double D[3][5];
     rotate_gradient(GLg, e, D);
-    side_terms<1>(D, wl, gl, K, gm1, tau, q4, q5, edt, dtf, dWc, Facc, Wacc, Iacc);
+    side_terms(D, wl, gl, ml0, ml1, K, gl.l2 * gl.l2 * iK3, gm1, tau, q4, q5, edt, dtf, dWc, Facc, Wacc, Iacc);
     rotate_gradient(GRg, e, D);
-    side_terms<-1>(D, wr, gr, K, gm1, tau, q4, q5, edt, dtf, dWc, Facc, Wacc, Iacc);
+    side_terms(D, wr, gr, mr0, mr1, K, gr.l2 * gr.l2 * iK3, gm1, tau, q4, q5, edt, dtf, dWc, Facc, Wacc, Iacc);
   }
   // equilibrium part: slopes a^c from the kinetic-weighted interface gradients; A^c from
   // <A + a.u> = 0; full-space moments through the Euler-flux Jacobians
+  const double ckc = gc.l2 * gc.l2 * iK3;
   double ac[3][5];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) slope_solve(gc, K, dWc[k], ac[k]);
-  double cu[5] = {0, 0, 0, 0, 0};  // <(a^c . u) psi>_c = sum_k J_k dW^c_k
+  for (int k = 0; k < 3; ++k) slope_solve(gc, ckc, dWc[k], ac[k]);
+  double cu[5];  // <(a^c . u) psi>_c = sum_k J_k dW^c_k
+  {
+    double t0[5], t1[5], t2[5];
+    euler_jvp(wc, gc, gm1, 0, dWc[0], t0);
+    euler_jvp(wc, gc, gm1, 1, dWc[1], t1);
+    euler_jvp(wc, gc, gm1, 2, dWc[2], t2);
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    double t[5];
-    euler_jvp(wc, gc, gm1, k, dWc[k], t);
-#pragma unroll
-    for (int q = 0; q < 5; ++q) cu[q] += t[q];
+    for (int q = 0; q < 5; ++q) cu[q] = t0[q] + t1[q] + t2[q];
   }
   double Fc0[5], FcA[5], Fca[5];
   {
     // <u psi>_c is the Euler flux of W^c; <u A^c psi>_c = J_n <A^c psi>_c = -J_n <(a^c . u) psi>_c
-    const double u0 = gc.U, pcc = pc;
     Fc0[0] = wc[1];
-    Fc0[1] = wc[1] * u0 + pcc;
-    Fc0[2] = wc[2] * u0;
-    Fc0[3] = wc[3] * u0;
-    Fc0[4] = (wc[4] + pcc) * u0;
+    Fc0[1] = wc[1] * gc.U + gc.p;
+    Fc0[2] = wc[2] * gc.U;
+    Fc0[3] = wc[3] * gc.U;
+    Fc0[4] = (wc[4] + gc.p) * gc.U;
     euler_jvp(wc, gc, gm1, 0, cu, FcA);
 #pragma unroll
     for (int q = 0; q < 5; ++q) FcA[q] = -FcA[q];
-    Mom M;
-    make_mom(gc, 0, K, M);
-    double xx[5], yy[5], zz[5];
-    psi_apply<2, 0, 0>(M, ac[0], xx);
-    psi_apply<1, 1, 0>(M, ac[1], yy);
-    psi_apply<1, 0, 1>(M, ac[2], zz);
+    // <u (a^c . u) psi>_c in the frame moving with the tangential velocity
+    MomP P;
+    make_momp(gc, 1.0, gc.U, K, P);
+    double a0[5], a1[5], a2[5], o[5];
+    to_primed(P, ac[0], a0);
+    to_primed(P, ac[1], a1);
+    to_primed(P, ac[2], a2);
+    papp_au<1>(P, a0, a1, a2, o);
 #pragma unroll
-    for (int q = 0; q < 5; ++q) Fca[q] = xx[q] + yy[q] + zz[q];
+    for (int q = 0; q < 5; ++q) Fca[q] = 0.0;
+    add_from_primed(P, o, 1.0, Fca);
   }
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
@@ -474,7 +558,7 @@ HD void gks_point_body(int64_t g, const PointArgs& a) {
                       Ub[0] * (Iacc[4] - (Ub[0] * Iacc[1] + Ub[1] * Iacc[2] + Ub[2] * Iacc[3]) + 0.5 * U2 * Iacc[0]);
     Facc[4] += (1.0 / ph.prandtl - 1.0) * qn;
   }
-  const double sdt = wgt / dtf;
+  const double sdt = 1.0 / (iw * dtf);  // weight / dt
 #pragma unroll
   for (int q = 0; q < 5; ++q) Facc[q] *= sdt;
   double Fg[5], Wg[5];
