@@ -52,16 +52,21 @@ def workload_name(w):
 
 
 def launches_per_vcycle(P, history=False):
-    """Kernels launched by one V-cycle (fine step, defect, restriction, coarse FAS levels, corrections)."""
+    """Kernels launched by one V-cycle (fine step, defect, restriction, coarse levels, corrections).
+    FP64 (FAS): a coarse level evaluates its KFVS residual at W^0 for the forcing and the first step
+    (faces + gather) plus the forcing kernel; mixed (defect correction): the first step needs no
+    residual (the defect is the restricted one) and later residuals are FP32 directional derivatives
+    (faces + gather)."""
     dtm = 2 if P["dt_mode"] == 1 else 0
     fine_step = 3 + dtm + (2 if history else 0)
     n = fine_step * max(P["pre"], 1)
     nl = P["n_levels"]
+    C = P["coarse_steps"]
     if nl > 1:
         n += 3 + dtm + 1  # defect (reconstruct, points, gather) + restriction
 
         def coarse(l):
-            k = 2 + 1 + P["coarse_steps"] * (2 + 1 + dtm + 1)
+            k = (0 if P["precision"] == 1 else 3) + C * (1 + dtm + 1) + (C - 1) * 2
             if l + 1 < nl:
                 k += 2 + 1 + coarse(l + 1) + 1 + P["post"] * (2 + 1 + dtm + 1)
             return k
@@ -266,6 +271,25 @@ def main():
     e2e_s = max_over_ranks(time.perf_counter() - t0)
     e2e = {"value": world * nc * args.steps / e2e_s / 1e6, "unit": UNIT,
            "h2d_bytes_per_step": int(Wh.numel() + Gh.numel() + ah.numel()) * 8, "d2h_bytes_per_step": 8}
+    # the mixed-precision V-cycle on the same workload: coarse levels in FP32 defect-correction form
+    ctx.set_params(cg.default_params(precision=1, **PARAMS))
+    ctx.state_init(Wd, Gd)
+    ctx.vcycle(args.warmup, history=False)
+    barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    ctx.vcycle(args.steps, history=False)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_mixed = max_over_ranks(ev0.elapsed_time(ev1))
+    Pm = ctx.params
+    mixed = {"value": world * nc * args.steps / (ms_mixed * 1e-3) / 1e6, "unit": UNIT,
+             "ms_per_step": ms_mixed / args.steps,
+             "gpu_launches": launches_per_vcycle({f: getattr(Pm, f) for f in (
+                 "dt_mode", "pre", "post", "n_levels", "coarse_steps", "precision")}) * args.steps,
+             "what": "3-level V-cycle, FP64 fine CGKS, coarse levels smoothing the correction with the "
+                     "FP32 linearised KFVS operator (precision 1)"}
     peak = cg.cgks_fp64_peak()
     k_avg = k_ms / max(k_n, 1)
     roofline = {"bound": "alu", "kernel": "k_gks_points (FP64 gas-kinetic flux per Gauss point)",
@@ -278,7 +302,8 @@ def main():
         roofline.update(achieved=ach, frac=ach / peak, flop_per_gauss_point=FLOP_PER_GP)
     if DRAM_BYTES_PER_GP:
         roofline["traffic"] = DRAM_BYTES_PER_GP * ngp
-    launches = launches_per_vcycle({f: getattr(P, f) for f in ("dt_mode", "pre", "post", "n_levels", "coarse_steps")})
+    launches = launches_per_vcycle({f: getattr(P, f) for f in ("dt_mode", "pre", "post", "n_levels", "coarse_steps",
+                                                               "precision")})
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded mesh, free-stream start)",
@@ -287,7 +312,8 @@ def main():
                       "parallelism": "replicas" if world > 1 else "single GPU",
                       "l2": "working set (~6 GB) far above L2 (129 MB); no flush needed",
                       "setup_s": setup_s, "params": {k: v for k, v in PARAMS.items()}},
-           "e2e": e2e, "gpu_launches": launches * args.steps, "roofline": roofline, "clocks": clk.summary()}
+           "e2e": e2e, "gpu_launches": launches * args.steps, "roofline": roofline, "clocks": clk.summary(),
+           "mixed": mixed}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
     ctx.close()

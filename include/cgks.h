@@ -59,7 +59,10 @@ typedef struct {
   int32_t passes_per_level; /* pairwise coarsening passes per multigrid level (2) */
   int32_t viscous;     /* 0 Euler, 1 Navier-Stokes (tau = mu/p) */
   int32_t dt_mode;     /* 0 local time steps, 1 one global (minimum) time step per level */
-  int32_t precision;   /* 0 FP64 on every level; 1 FP32 coarse levels (not available: EUNSUPPORTED) */
+  int32_t precision;   /* 0 FP64 on every level (FAS coarse equations); 1 mixed: the coarse levels smooth
+                          the correction W - W^0 with the FP32 linearised KFVS operator (defect
+                          correction, cgks_kfvs_jvp); the fine level, the defect, its restriction,
+                          the states, updates and correction stay FP64 */
   uint64_t agglo_seed; /* 0: the paper's hash on cell ids; s > 0 relabels cell N as splitmix64(N ^ s) >> 33 */
 } cgks_params;
 
@@ -135,6 +138,13 @@ cgks_status cgks_residual(cgks_ctx* ctx, int order, double* res, double* gradW_n
 
 /* First-order KFVS residual of level `level` for the state W double[5][n_level] (device in/out). */
 cgks_status cgks_kfvs_residual(cgks_ctx* ctx, int level, const double* W, double* res);
+
+/* Directional derivative out = J(W0) dW of the KFVS residual of level `level` (the Jacobian of
+ * cgks_kfvs_residual at W0, boundary ghost states included), evaluated in FP32 forward mode with
+ * FP64 sums over each cell's faces.  This is the coarse-level operator of the mixed-precision
+ * V-cycle (precision 1): the coarse equations of Sec. 4.2 in defect-correction form.  W0, dW, out:
+ * device double[5][n_level]; out may not alias W0 or dW.  CGKS_ENAN if W0 is not a physical state. */
+cgks_status cgks_kfvs_jvp(cgks_ctx* ctx, int level, const double* W0, const double* dW, double* out);
 
 /* n_steps explicit single-grid CGKS steps (Eq. smo).  norm_hist: host double[n_steps] of the
  * residual norm before each step (nullable; synchronises).  CGKS_ENAN if a state becomes

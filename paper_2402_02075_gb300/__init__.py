@@ -23,7 +23,7 @@ STATUS = {0: "CGKS_OK", 1: "CGKS_EINVAL", 2: "CGKS_ENOMEM", 3: "CGKS_ECUDA", 4: 
 # every entry point declared in include/cgks.h
 EXPORTS = ["cgks_default_params", "cgks_create", "cgks_destroy", "cgks_set_params", "cgks_mesh_upload",
            "cgks_level_info", "cgks_coarse_map", "cgks_level_geometry", "cgks_fine_moments", "cgks_state_init",
-           "cgks_state_get", "cgks_residual", "cgks_kfvs_residual", "cgks_step", "cgks_vcycle", "cgks_steady_solve",
+           "cgks_state_get", "cgks_residual", "cgks_kfvs_residual", "cgks_kfvs_jvp", "cgks_step", "cgks_vcycle", "cgks_steady_solve",
            "cgks_adjoint", "cgks_fp64_peak", "cgks_profile", "cgks_kernel_stats", "cgks_density_norm_noalloc",
            "cgks_last_error"]
 
@@ -65,6 +65,7 @@ def load(path: str = LIB_PATH):
             "cgks_state_get": [P, d, d, d],
             "cgks_residual": [P, C.c_int, d, d, d, d, C.POINTER(C.c_double)],
             "cgks_kfvs_residual": [P, C.c_int, d, d],
+            "cgks_kfvs_jvp": [P, C.c_int, d, d, d],
             "cgks_step": [P, C.c_int, C.POINTER(C.c_double)],
             "cgks_vcycle": [P, C.c_int, C.POINTER(C.c_double)],
             "cgks_steady_solve": [P, C.c_int, C.c_double, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_double),
@@ -211,6 +212,12 @@ class Context:
         res = self.torch.empty_like(W)
         _check(load().cgks_kfvs_residual(self.h, level, _ptr(W), _ptr(res)), self.h)
         return res
+
+    def kfvs_jvp(self, level, W0, dW):
+        """J(W0) dW of the level's KFVS residual (FP32 forward mode, FP64 sums)."""
+        out = self.torch.empty_like(W0)
+        _check(load().cgks_kfvs_jvp(self.h, level, _ptr(W0), _ptr(dW), _ptr(out)), self.h)
+        return out
 
     def step(self, n=1, history=True):
         h = np.zeros(max(n, 1))

@@ -467,6 +467,7 @@ cgks_status build_levels(cgks_ctx* ctx) {
     CKS(dalloc(ctx, M, &B.R, 5 * n));
     CKS(dalloc(ctx, M, &B.dt, n));
     CKS(dalloc(ctx, M, &B.ff, 5 * ctx->L[l].nf));
+    CKS(dalloc(ctx, M, &B.ff32, 5 * ctx->L[l].nf));
   }
   CK(cudaGetLastError());
   return CGKS_OK;

@@ -250,7 +250,7 @@ static cgks_status check_params(cgks_ctx* ctx, const cgks_params* p) {
   if (!(p->prandtl > 0.0) || !(p->weno_eps > 0.0)) return cgks_fail(ctx, CGKS_EINVAL, "prandtl/weno_eps");
   if (p->n_levels < 1 || p->n_levels > 8 || p->passes_per_level < 0 || p->coarse_steps < 0 || p->pre < 0 || p->post < 0)
     return cgks_fail(ctx, CGKS_EINVAL, "multigrid counts out of range");
-  if (p->precision != 0) return cgks_fail(ctx, CGKS_EUNSUPPORTED, "only precision 0 (FP64) is available");
+  if (p->precision != 0 && p->precision != 1) return cgks_fail(ctx, CGKS_EINVAL, "precision must be 0 or 1");
   return CGKS_OK;
 }
 
@@ -347,6 +347,7 @@ cgks_status cgks_mesh_upload(cgks_ctx* ctx, int64_t n_nodes, const double* xyz, 
   CKS(dalloc(ctx, M, &ctx->gpW, 5 * F.ngp));
   CKS(dalloc(ctx, M, &ctx->gpa, F.ngp));
   CKS(dalloc(ctx, M, &ctx->ffl, 5 * F.nf));
+  CKS(dalloc(ctx, M, &ctx->ffl32, 5 * F.nf));
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->has_mesh = true;
   return CGKS_OK;
@@ -474,6 +475,14 @@ cgks_status cgks_kfvs_residual(cgks_ctx* ctx, int level, const double* W, double
     return cgks_fail(ctx, CGKS_EINVAL, "cgks_kfvs_residual: bad level or NULL array");
   CKS(kfvs_residual(ctx, level, W, res));
   return check_device_error(ctx, "cgks_kfvs_residual");
+}
+
+cgks_status cgks_kfvs_jvp(cgks_ctx* ctx, int level, const double* W0, const double* dW, double* out) {
+  NEED_MESH();
+  if (level < 0 || level >= (int)ctx->L.size() || !W0 || !dW || !out)
+    return cgks_fail(ctx, CGKS_EINVAL, "cgks_kfvs_jvp: bad level or NULL array");
+  CKS(kfvs_jvp(ctx, level, W0, dW, 0, out));
+  return check_device_error(ctx, "cgks_kfvs_jvp");
 }
 
 static cgks_status run_iterations(cgks_ctx* ctx, int n, double* norm_hist, bool multigrid, const char* name) {

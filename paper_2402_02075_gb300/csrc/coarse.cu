@@ -5,6 +5,7 @@
 #include "internal.cuh"
 #include "kinetic.cuh"
 
+// KFVS face fluxes x area (FP64)
 __global__ void k_kfvs_faces(int64_t nf, const int32_t* __restrict__ fL, const int32_t* __restrict__ fR,
                              const int32_t* __restrict__ ftag, const double* __restrict__ Sn, int64_t nc,
                              const double* __restrict__ W, double* __restrict__ ff, Phys ph, DevErr* err) {
@@ -28,10 +29,45 @@ __global__ void k_kfvs_faces(int64_t nf, const int32_t* __restrict__ fL, const i
   for (int q = 0; q < 5; ++q) ff[q * nf + f] = s * F[q];
 }
 
-// res = -(sum of outward face fluxes); optional forcing F and explicit update W += dt/V (res + F)
+// Directional derivative of the KFVS face fluxes x area at the state W0 in the direction dW, in
+// FP32 forward mode: dW = X - W0 when x_is_state, else X.  The boundary ghost state is
+// differentiated with the cell state it is built from.
+__global__ void k_kfvs_jvp_faces(int64_t nf, const int32_t* __restrict__ fL, const int32_t* __restrict__ fR,
+                                 const int32_t* __restrict__ ftag, const double* __restrict__ Sn, int64_t nc,
+                                 const double* __restrict__ W0, const double* __restrict__ X, int x_is_state,
+                                 float* __restrict__ ff, Phys ph, DevErr* err) {
+  using D = Dual<float>;
+  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= nf) return;
+  const float S[3] = {float(Sn[f]), float(Sn[nf + f]), float(Sn[2 * nf + f])};
+  const float s = sqrtf(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+  const D n[3] = {D(S[0] / s), D(S[1] / s), D(S[2] / s)};
+  const int64_t L = fL[f], R = fR[f];
+  D WL[5], WR[5], F[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    const double w = W0[q * nc + L], x = X[q * nc + L];
+    WL[q] = D(float(w), float(x_is_state ? x - w : x));
+  }
+  if (R >= 0) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      const double w = W0[q * nc + R], x = X[q * nc + R];
+      WR[q] = D(float(w), float(x_is_state ? x - w : x));
+    }
+  } else if (!bc_ghost<D>(ftag[f], n, WL, nullptr, WR, nullptr, D(ph.gamma), ph.Winf)) {
+    set_err(err, CGKS_ENAN, (int)L, 23);
+  }
+  if (!kfvs_flux<D>(WL, WR, n, D(ph.K), D(ph.gamma - 1.0), F)) set_err(err, CGKS_ENAN, (int)L, 24);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) ff[q * nf + f] = s * F[q].d;
+}
+
+// res = -(sum of outward face fluxes), summed in FP64 in ascending face order
+template <typename T>
 __global__ void k_kfvs_gather(int64_t nc, int64_t nf, const int32_t* __restrict__ ptr, const int32_t* __restrict__ c2f,
                               const int32_t* __restrict__ fL, const int32_t* __restrict__ fR,
-                              const double* __restrict__ ff, double* __restrict__ res) {
+                              const T* __restrict__ ff, double* __restrict__ res) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= nc) return;
   double r[5] = {0, 0, 0, 0, 0};
@@ -41,7 +77,7 @@ __global__ void k_kfvs_gather(int64_t nc, int64_t nf, const int32_t* __restrict_
     if (a == b) continue;  // a cell's periodic image of itself: the two sides cancel
     const double s = a == c ? 1.0 : -1.0;
 #pragma unroll
-    for (int q = 0; q < 5; ++q) r[q] -= s * ff[q * nf + f];
+    for (int q = 0; q < 5; ++q) r[q] -= s * (double)ff[q * nf + f];
   }
 #pragma unroll
   for (int q = 0; q < 5; ++q) res[q * nc + c] = r[q];
@@ -169,12 +205,24 @@ cgks_status density_norm(cgks_ctx* ctx, const double* res, const double* vol, in
 
 cgks_status global_min_dt(cgks_ctx* ctx, double* dt, int64_t n);
 
+// KFVS residual of level `lev` (FP64)
 cgks_status kfvs_residual(cgks_ctx* ctx, int lev, const double* W, double* res) {
   const Level& L = ctx->L[lev];
   const Phys ph = make_phys(ctx->P);
   double* ff = lev == 0 ? ctx->ffl : ctx->C[lev].ff;
   k_kfvs_faces<<<grid_for(L.nf, 256), 256, 0, ctx->stream>>>(L.nf, L.fL, L.fR, L.ftag, L.Sn, L.nc, W, ff, ph, ctx->derr);
-  k_kfvs_gather<<<grid_for(L.nc, 256), 256, 0, ctx->stream>>>(L.nc, L.nf, L.c2f_ptr, L.c2f, L.fL, L.fR, ff, res);
+  k_kfvs_gather<double><<<grid_for(L.nc, 256), 256, 0, ctx->stream>>>(L.nc, L.nf, L.c2f_ptr, L.c2f, L.fL, L.fR, ff, res);
+  CK(cudaGetLastError());
+  return CGKS_OK;
+}
+
+cgks_status kfvs_jvp(cgks_ctx* ctx, int lev, const double* W0, const double* X, int x_is_state, double* res) {
+  const Level& L = ctx->L[lev];
+  const Phys ph = make_phys(ctx->P);
+  float* ff = lev == 0 ? ctx->ffl32 : ctx->C[lev].ff32;
+  k_kfvs_jvp_faces<<<grid_for(L.nf, 256), 256, 0, ctx->stream>>>(L.nf, L.fL, L.fR, L.ftag, L.Sn, L.nc, W0, X,
+                                                                  x_is_state, ff, ph, ctx->derr);
+  k_kfvs_gather<float><<<grid_for(L.nc, 256), 256, 0, ctx->stream>>>(L.nc, L.nf, L.c2f_ptr, L.c2f, L.fL, L.fR, ff, res);
   CK(cudaGetLastError());
   return CGKS_OK;
 }
@@ -190,22 +238,49 @@ cgks_status coarse_dt(cgks_ctx* ctx, int lev, const double* W, double* dt) {
 
 // coarse-level FAS smoothing on level l with the restricted state already in C[l].W (and W0) and
 // the restricted defect in C[l].Rs, then recursion to the next level and correction
+// coarse-level residual at the current state B.W into B.R, the defect being B.R + B.F:
+// FP64 FAS: R = Res(W), F = Res* - Res(W^0);  precision 1 (defect correction): R = J(W^0)(W - W^0)
+// in FP32 forward mode, F = Res*, so the defect is linear in the correction W - W^0 and FP32 only
+// perturbs it relative to its own size
+static cgks_status coarse_residual(cgks_ctx* ctx, int l) {
+  CoarseBuf& B = ctx->C[l];
+  if (ctx->P.precision == 1) return kfvs_jvp(ctx, l, B.W0, B.W, 1, B.R);
+  return kfvs_residual(ctx, l, B.W, B.R);
+}
+
+static cgks_status coarse_smooth(cgks_ctx* ctx, int l) {
+  const Level& L = ctx->L[l];
+  CoarseBuf& B = ctx->C[l];
+  CKS(coarse_dt(ctx, l, B.W, B.dt));
+  k_fe_update<<<grid_for(L.nc, 256), 256, 0, ctx->stream>>>(L.nc, B.dt, L.vol, B.R, B.F, B.W, ctx->P.gamma,
+                                                             ctx->derr);
+  CK(cudaGetLastError());
+  return CGKS_OK;
+}
+
+// coarse level l of the V-cycle, entered with W = W^0 (the restricted state) and Res* (the
+// restricted defect)
 static cgks_status coarse_cycle(cgks_ctx* ctx, int l) {
   const Level& L = ctx->L[l];
   CoarseBuf& B = ctx->C[l];
   cudaStream_t st = ctx->stream;
   const int64_t n5 = 5 * L.nc;
-  CKS(kfvs_residual(ctx, l, B.W, B.R));
-  k_forcing<<<grid_for(n5, 256), 256, 0, st>>>(n5, B.Rs, B.R, B.F);
-  for (int s = 0; s < ctx->P.coarse_steps; ++s) {
+  // the residual at W = W^0 serves the forcing and the first step
+  if (ctx->P.precision == 1) {
+    CK(cudaMemcpyAsync(B.F, B.Rs, sizeof(double) * n5, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemsetAsync(B.R, 0, sizeof(double) * n5, st));
+  } else {
     CKS(kfvs_residual(ctx, l, B.W, B.R));
-    CKS(coarse_dt(ctx, l, B.W, B.dt));
-    k_fe_update<<<grid_for(L.nc, 256), 256, 0, st>>>(L.nc, B.dt, L.vol, B.R, B.F, B.W, ctx->P.gamma, ctx->derr);
+    k_forcing<<<grid_for(n5, 256), 256, 0, st>>>(n5, B.Rs, B.R, B.F);
+  }
+  for (int s = 0; s < ctx->P.coarse_steps; ++s) {
+    if (s > 0) CKS(coarse_residual(ctx, l));
+    CKS(coarse_smooth(ctx, l));
   }
   if (l + 1 < (int)ctx->L.size()) {
     const Level& Cn = ctx->L[l + 1];
     CoarseBuf& N = ctx->C[l + 1];
-    CKS(kfvs_residual(ctx, l, B.W, B.R));
+    CKS(coarse_residual(ctx, l));
     k_restrict<<<grid_for(Cn.nc, 256), 256, 0, st>>>(Cn.nc, L.nc, Cn.agg_ptr, Cn.agg, L.vol, Cn.vol, B.W, B.R, B.F,
                                                      N.W, N.Rs);
     CK(cudaMemcpyAsync(N.W0, N.W, sizeof(double) * 5 * Cn.nc, cudaMemcpyDeviceToDevice, st));
@@ -213,9 +288,8 @@ static cgks_status coarse_cycle(cgks_ctx* ctx, int l) {
     k_prolong<<<grid_for(L.nc, 256), 256, 0, st>>>(L.nc, Cn.nc, Cn.f2c, N.W, N.W0, B.W, ctx->P.gamma,
                                                    (unsigned long long*)ctx->d_count);
     for (int s = 0; s < ctx->P.post; ++s) {
-      CKS(kfvs_residual(ctx, l, B.W, B.R));
-      CKS(coarse_dt(ctx, l, B.W, B.dt));
-      k_fe_update<<<grid_for(L.nc, 256), 256, 0, st>>>(L.nc, B.dt, L.vol, B.R, B.F, B.W, ctx->P.gamma, ctx->derr);
+      CKS(coarse_residual(ctx, l));
+      CKS(coarse_smooth(ctx, l));
     }
   }
   CK(cudaGetLastError());

@@ -73,6 +73,7 @@ struct Fine {
 
 struct CoarseBuf {  // per coarse level work arrays
   double *W = nullptr, *W0 = nullptr, *Rs = nullptr, *F = nullptr, *R = nullptr, *dt = nullptr, *ff = nullptr;
+  float* ff32 = nullptr;  // FP32 directional derivatives of the face fluxes (precision 1)
 };
 
 struct cgks_ctx {
@@ -90,6 +91,7 @@ struct cgks_ctx {
   double *gpF = nullptr, *gpW = nullptr, *gpa = nullptr;
   double *W1 = nullptr;             // copy of W used by the V-cycle
   double *ffl = nullptr;            // first-order face fluxes of level 0
+  float* ffl32 = nullptr;           // their FP32 directional derivatives
   double *nrm_part = nullptr, *nrm = nullptr, *h_nrm = nullptr;
   DevErr* derr = nullptr;
   DevErr* h_err = nullptr;
@@ -159,6 +161,9 @@ cgks_status density_norm(cgks_ctx* ctx, const double* res, const double* vol, in
 
 // first-order (KFVS) residual of a level; res may equal nullptr when only the face fluxes are needed
 cgks_status kfvs_residual(cgks_ctx* ctx, int lev, const double* W, double* res);
+// res = J(W0) dW, J the Jacobian of the KFVS residual of level `lev`, in FP32 forward mode with FP64
+// sums; dW = X - W0 when x_is_state, else X
+cgks_status kfvs_jvp(cgks_ctx* ctx, int lev, const double* W0, const double* X, int x_is_state, double* res);
 cgks_status coarse_dt(cgks_ctx* ctx, int lev, const double* W, double* dt);
 cgks_status vcycle_once(cgks_ctx* ctx, double* norm_dev);
 cgks_status step_once(cgks_ctx* ctx, double* norm_dev);

@@ -29,6 +29,68 @@ template <>
 HD double terfc<double>(double x) { return erfc(x); }
 template <>
 HD float terfc<float>(float x) { return erfcf(x); }
+// x^y for an exponent y that is a constant of the model (gamma, 1/(gamma - 1))
+template <typename T>
+HD T tpow(T x, T y);
+template <>
+HD double tpow<double>(double x, double y) { return pow(x, y); }
+template <>
+HD float tpow<float>(float x, float y) { return powf(x, y); }
+
+// Forward-mode derivative: value v and directional derivative d of every quantity, so that one
+// evaluation of a model function on Dual inputs (W, dW) yields f(W) and J(W) dW.  Comparisons act
+// on values; constants (normals, gamma, the free stream) carry d = 0.
+template <typename S>
+struct Dual {
+  S v, d;
+  Dual() = default;
+  HD Dual(S v_, S d_) : v(v_), d(d_) {}
+  HD Dual(double c) : v(S(c)), d(S(0)) {}
+  HD Dual(float c) : v(S(c)), d(S(0)) {}
+  HD Dual(int c) : v(S(c)), d(S(0)) {}
+};
+template <typename S>
+HD Dual<S> operator+(Dual<S> a, Dual<S> b) { return {a.v + b.v, a.d + b.d}; }
+template <typename S>
+HD Dual<S> operator-(Dual<S> a, Dual<S> b) { return {a.v - b.v, a.d - b.d}; }
+template <typename S>
+HD Dual<S> operator-(Dual<S> a) { return {-a.v, -a.d}; }
+template <typename S>
+HD Dual<S> operator*(Dual<S> a, Dual<S> b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
+template <typename S>
+HD Dual<S> operator/(Dual<S> a, Dual<S> b) {
+  const S q = a.v / b.v;
+  return {q, (a.d - q * b.d) / b.v};
+}
+template <typename S>
+HD Dual<S>& operator+=(Dual<S>& a, Dual<S> b) { return a = a + b; }
+template <typename S>
+HD bool operator<(Dual<S> a, Dual<S> b) { return a.v < b.v; }
+template <typename S>
+HD bool operator>(Dual<S> a, Dual<S> b) { return a.v > b.v; }
+template <typename S>
+HD bool operator<=(Dual<S> a, Dual<S> b) { return a.v <= b.v; }
+template <typename S>
+HD bool operator>=(Dual<S> a, Dual<S> b) { return a.v >= b.v; }
+template <>
+HD Dual<float> tsqrt<Dual<float>>(Dual<float> x) {
+  const float r = sqrtf(x.v);
+  return {r, 0.5f * x.d / r};
+}
+template <>
+HD Dual<float> texp<Dual<float>>(Dual<float> x) {
+  const float e = expf(x.v);
+  return {e, e * x.d};
+}
+template <>
+HD Dual<float> terfc<Dual<float>>(Dual<float> x) {  // erfc'(x) = -2/sqrt(pi) exp(-x^2)
+  return {erfcf(x.v), -1.1283791670955126f * expf(-x.v * x.v) * x.d};
+}
+template <>
+HD Dual<float> tpow<Dual<float>>(Dual<float> x, Dual<float> y) {  // y constant
+  const float p = powf(x.v, y.v);
+  return {p, y.v * p / x.v * x.d};
+}
 
 // branchless orthonormal basis (t1, t2) completing the unit normal n (Duff et al., JCGT 6(1), 2017)
 template <typename T>
@@ -199,15 +261,15 @@ HD bool bc_ghost(int tag, const T n[3], const T W[5], const T* G, T Wg[5], T* Gg
     const T unb = T(0.5) * (Rp + Rm), cb = T(0.25) * gm1 * (Rp - Rm);
     T s, ut[3];
     if (unb > T(0)) {
-      s = p / pow(rho, gamma);
+      s = p / tpow(rho, gamma);
 #pragma unroll
       for (int d = 0; d < 3; ++d) ut[d] = u[d] - un * n[d];
     } else {
-      s = pi / pow(ri, gamma);
+      s = pi / tpow(ri, gamma);
 #pragma unroll
       for (int d = 0; d < 3; ++d) ut[d] = ui[d] - uni * n[d];
     }
-    const T rb = pow(cb * cb / (gamma * s), T(1) / gm1);
+    const T rb = tpow(cb * cb / (gamma * s), T(1) / gm1);
     const T pb = rb * cb * cb / gamma;
     T ub[3], u2 = T(0);
 #pragma unroll

@@ -148,8 +148,8 @@ def test_error_paths(cg):
         cg.Context(cg.default_params(gamma=0.9))
     assert e.value.status == 1
     with pytest.raises(cg.CgksError) as e:
-        cg.Context(cg.default_params(precision=1))
-    assert e.value.status == 8
+        cg.Context(cg.default_params(precision=2))
+    assert e.value.status == 1
     mesh = mg.periodic_box(4)
     ctx = cg.Context(cg.default_params())
     with pytest.raises(cg.CgksError) as e:
