@@ -3,11 +3,14 @@
 
 A step is one 3-level V-cycle (Sec. 4.2 of the paper: a CGKS pre-smoothing step, the defect at the
 new state, KFVS forward-Euler smoothing with FAS forcing on the two agglomerated levels, injection
-correction) on the laminar boundary-layer box: 96 x 64 x 64 grid split into 35 wall layers of prisms
-and Kuhn tetrahedra above (1,499,136 cells), no-slip wall, farfield, Mach 0.5, Re 1e4, Pr 0.72,
-seeded synthetic mesh and free-stream start.  The metric is fine cells x V-cycles per second.
+correction) on the laminar boundary-layer box: 96 x 64 x 64 grid, wall-normal grading 1e-4 x 1.1
+(capped at 2 dx), 42 wall layers of prisms and Kuhn tetrahedra above (1,327,104 cells), no-slip wall,
+farfield, Mach 0.5, Re 1e4, Pr 0.72, seeded synthetic mesh and free-stream start.  The metric is
+fine cells x V-cycles per second, for the FP64 V-cycle (value) and the mixed-precision one (mixed);
+`converge` reports wall times to a 1e-10 residual drop of single-grid FP64, FP64 V-cycle and mixed
+V-cycle on small cases (--converge-slab adds the 96 x 4 x 64 slab of the workload's layout).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--converge-slab]
 
 Multi-GPU: one process per GPU (torchrun); each rank runs an independent replica (the method is
 not partitioned in this build), the step time is the maximum over ranks and the value counts the
@@ -30,12 +33,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Mcell-iters/s; wall time to 1e-10 residual drop: FP64 vs mixed V-cycle"
 UNIT = "Mcell-iters/s"
-WORKLOAD = dict(nx=96, ny=64, nz=64, n_prism=35)
+WORKLOAD = dict(nx=96, ny=64, nz=64)
 PARAMS = dict(mach=0.5, reynolds=1e4, prandtl=0.72, gamma=1.4, viscous=1, n_levels=3, cfl_fine=0.5,
               cfl_coarse=0.5, agglo_seed=0)
-# bounded sample of the same workload for the CPU oracle: the same layout and physics at 32 x 24 x 24
-# with 13 prism layers (70,656 cells)
-SAMPLE = dict(nx=32, ny=24, nz=24, n_prism=13)
+# bounded sample of the same workload for the CPU oracle: 4 of its 64 periodic columns in y, i.e. the
+# same x-z layout and physics (82,944 cells)
+SAMPLE = dict(nx=96, ny=4, nz=64)
 # FP64 floating-point operations per Gauss point of the gas-kinetic flux kernel (2 per DFMA, 1 per
 # DADD/DMUL), from the ncu instruction counts of a full capture of the kernel on the 48x32x32 box;
 # the kernel's own arithmetic, all of which the method needs
@@ -46,9 +49,11 @@ DRAM_BYTES_PER_GP = 191.5
 
 
 def workload_name(w):
-    cells = w["nx"] * w["ny"] * (2 * w["n_prism"] + 6 * (w["nz"] - w["n_prism"]))
+    import meshgen as mg
+    _, npz = mg.wall_layout(w["nx"], w["nz"])
+    cells = w["nx"] * w["ny"] * (2 * npz + 6 * (w["nz"] - npz))
     return (f"3-level FP64 V-cycle, laminar boundary-layer box {w['nx']}x{w['ny']}x{w['nz']} "
-            f"({cells:,} cells: {w['n_prism']} prism layers + Kuhn tetrahedra), M 0.5, Re 1e4, Pr 0.72")
+            f"({cells:,} cells: {npz} prism layers + Kuhn tetrahedra), M 0.5, Re 1e4, Pr 0.72")
 
 
 def launches_per_vcycle(P, history=False):
@@ -131,7 +136,7 @@ def dist_env():
     return rank, world, local
 
 
-def cpu_baseline(steps_per_sample=2):
+def cpu_baseline(steps_per_sample=6):
     """The oracle (as it stands) on a bounded sample of the workload: V-cycles per second x cells."""
     import meshgen as mg
     import oracle
@@ -151,6 +156,55 @@ def cpu_baseline(steps_per_sample=2):
             "sample": f"{steps_per_sample} V-cycles of the same layout and physics at "
                       f"{SAMPLE['nx']}x{SAMPLE['ny']}x{SAMPLE['nz']} ({M.nc:,} cells), after 1 warm-up cycle",
             "seconds": dt}
+
+
+def _state_diff(Wa, Wb):
+    """max |Wa - Wb| over each variable's largest |Wb| (momentum components share one scale)."""
+    import numpy as np
+    sw = np.abs(Wb).max(axis=1)
+    sw[1:4] = sw[1:4].max()
+    return float((np.abs(Wa - Wb).max(axis=1) / sw).max())
+
+
+def converge_cases(slab):
+    """Cases driven to a 1e-10 residual drop: (name, mesh factory, physics, max iterations)."""
+    import meshgen as mg
+    vis = dict(mach=0.5, reynolds=1e4, prandtl=0.72, viscous=1)
+    cases = [("Mach 3 compression ramp 48x24x4, 3 prism layers + hexahedra, inviscid",
+              lambda: mg.ramp_box(48, 24, 4, n_prism=3), dict(mach=3.0), 20000),
+             ("boundary layer 24x4x24 (first 1e-3, ratio 1.2), 17 prism layers + Kuhn tetrahedra, M 0.5, Re 1e4",
+              lambda: mg.wall_box(24, 4, 24, first=1e-3, ratio=1.2), vis, 100000)]
+    if slab:
+        cases.append(("the workload's layout on a 96x4x64 slab (4 periodic columns), M 0.5, Re 1e4",
+                      lambda: mg.wall_box(96, 4, 64), vis, 400000))
+    return cases
+
+
+def run_converge(cg, torch, slab):
+    """Wall time (host clock around the library's own steady-solve loop) to a 1e-10 drop of the
+    density residual for single-grid FP64 CGKS, the FP64 V-cycle and the mixed V-cycle."""
+    import numpy as np
+    import meshgen as mg
+    out = []
+    for name, mk, phys, max_it in converge_cases(slab):
+        mesh = mk()
+        row = {"case": name, "cells": len(mesh["cell_type"])}
+        states = {}
+        for key, mgrid, prec in (("single_grid_fp64", False, 0), ("vcycle_fp64", True, 0), ("vcycle_mixed", True, 1)):
+            P = cg.default_params(n_levels=3, precision=prec, **phys)
+            ctx = cg.upload_mesh(mesh, P)
+            W, G = mg.uniform_state(ctx.nc, mach=phys["mach"])
+            ctx.state_init(torch.from_numpy(W).cuda(), torch.from_numpy(G).cuda())
+            torch.cuda.synchronize()
+            r = ctx.steady_solve(multigrid=mgrid, drop=1e-10, max_iters=max_it, raise_on_notconv=False)
+            states[key] = ctx.state_get()[0].cpu().numpy()
+            row[key] = {"iters": r["iters"], "seconds": r["seconds"], "drop": r["drop"], "converged": r["converged"]}
+            ctx.close()
+        row["state_diff_mixed_vs_fp64_vcycle"] = _state_diff(states["vcycle_mixed"], states["vcycle_fp64"])
+        row["state_diff_vcycle_vs_single_grid"] = _state_diff(states["vcycle_fp64"], states["single_grid_fp64"])
+        out.append(row)
+    return {"target_drop": 1e-10, "clock": "host wall time around cgks_steady_solve (checks the drop every 10 "
+            "iterations)", "cases": out}
 
 
 def run_reference(args):
@@ -189,12 +243,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--converge-slab", action="store_true",
+                    help="also drive the 96x4x64 slab of the workload's layout to 1e-10 (several minutes)")
+    ap.add_argument("--no-converge", action="store_true")
     ap.add_argument("--size", default="full", choices=["full", "small"],
                     help="small: the same layout at 48x32x32 (profiling captures only)")
     args = ap.parse_args()
     global WORKLOAD
     if args.size == "small":
-        WORKLOAD = dict(nx=48, ny=32, nz=32, n_prism=18)
+        WORKLOAD = dict(nx=48, ny=32, nz=32)
     if args.impl == "reference":
         run_reference(args)
         return
@@ -314,6 +371,8 @@ def main():
                       "setup_s": setup_s, "params": {k: v for k, v in PARAMS.items()}},
            "e2e": e2e, "gpu_launches": launches * args.steps, "roofline": roofline, "clocks": clk.summary(),
            "mixed": mixed}
+    if rank == 0 and world == 1 and not args.no_converge:
+        out["converge"] = run_converge(cg, torch, args.converge_slab)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
     ctx.close()

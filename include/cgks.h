@@ -63,12 +63,13 @@ typedef struct {
                           the correction W - W^0 with the FP32 linearised KFVS operator (defect
                           correction, cgks_kfvs_jvp); the fine level, the defect, its restriction,
                           the states, updates and correction stay FP64 */
+  int32_t coarse_smoother; /* 0 forward Euler (Sec. 4.2); 1 LU-SGS, the implicit variant of Sec. 4.3 */
   uint64_t agglo_seed; /* 0: the paper's hash on cell ids; s > 0 relabels cell N as splitmix64(N ^ s) >> 33 */
 } cgks_params;
 
 /* Fills *p with the defaults listed above (gamma 1.4, mach 0.2, reynolds 1e4, prandtl 1, aoa 0,
  * cfl 0.5/0.5, eps 0.01, C 1, weno 1e-5, skew 0.2, 3 levels, pre 1, post 0, 1 coarse step,
- * 2 passes, inviscid, local time steps, FP64, seed 0).  Host pointer. */
+ * 2 passes, inviscid, local time steps, FP64, forward-Euler coarse smoother, seed 0).  Host pointer. */
 cgks_status cgks_default_params(cgks_params* p);
 
 /* Creates a context on the current CUDA device.  params: host pointer, copied.  stream: a
@@ -161,6 +162,18 @@ cgks_status cgks_vcycle(cgks_ctx* ctx, int n_cycles, double* norm_hist);
  * CGKS_ENOTCONV when max_iters is reached first. */
 cgks_status cgks_steady_solve(cgks_ctx* ctx, int multigrid, double drop, int64_t max_iters, int64_t* iters_done,
                               double* final_drop, double* seconds);
+
+/* Colours of the LU-SGS sweep order of coarse level `level` (>= 1): Jones-Plassmann rounds on
+ * priorities (splitmix64(cell id), cell id), each cell taking the smallest colour none of its
+ * face neighbours has; the sweeps visit colour 0, 1, ... forward and back.  colors: int32[n_level]
+ * (host or device, nullable); n_colors: host, nullable.  Built on first use; synchronises. */
+cgks_status cgks_coarse_colors(cgks_ctx* ctx, int level, int32_t* colors, int32_t* n_colors);
+
+/* Number of cell updates skipped by the positivity rule since the last cgks_state_init: coarse
+ * forward-Euler updates and fine/coarse injection corrections that would have made rho or p
+ * non-positive leave that cell unchanged (Sec. 4.2 gives no rule; skipping keeps the cycle going
+ * through the start-up transient).  Synchronises. */
+cgks_status cgks_skipped_updates(cgks_ctx* ctx, int64_t* count);
 
 /* Discrete adjoint of the residual (extension, not in the paper).  Returns CGKS_EUNSUPPORTED. */
 cgks_status cgks_adjoint(cgks_ctx* ctx, const double* wall_disp_modes, int n_modes, double* dJ_dmodes,

@@ -276,18 +276,46 @@ def periodic_box(n=16, jitter=0.05, seed=2402, split=None):
                     jitter=jitter, seed=seed)
 
 
-def wall_box(nx=96, ny=64, nz=64, n_prism=35, first=1e-4, ratio=1.1, jitter=0.0, seed=2402):
-    """Laminar boundary-layer box: x in [0,1], y periodic with dy = dx, z graded from a
-    no-slip wall (first spacing `first`, growth `ratio`); n_prism prism_z layers at the wall
-    and Kuhn tets above; farfield on x-in, x-out and top.  96x64x64 -> 1,499,136 cells."""
+def wall_layout(nx=96, nz=64, first=1e-4, ratio=1.1, tet_min=0.5, tet_max=2.0):
+    """Wall-normal grid lines of the boundary-layer box and its number of prism layers: geometric
+    growth from `first` by `ratio` until the spacing reaches tet_max * dx (then uniform), prism
+    layers while the spacing is below tet_min * dx and Kuhn tetrahedra above, so that every
+    tetrahedron is within tet_max : 1 and 1 : 1/tet_min of the in-plane spacing dx = 1/nx."""
+    dx = 1.0 / nx
+    z = _graded(nz, first, ratio)
+    dz = np.diff(z)
+    if (dz >= tet_max * dx).any():
+        k = int(np.argmax(dz >= tet_max * dx))
+        z = np.concatenate([z[:k + 1], z[k] + tet_max * dx * np.arange(1, nz - k + 1)])
+        dz = np.diff(z)
+    n_prism = int(np.argmax(dz >= tet_min * dx)) if (dz >= tet_min * dx).any() else nz
+    return z, n_prism
+
+
+def wall_box(nx=96, ny=64, nz=64, n_prism=None, first=1e-4, ratio=1.1, jitter=0.0, seed=2402):
+    """Laminar boundary-layer box: x in [0,1], y periodic with dy = dx, z from a no-slip wall
+    (first spacing `first`, growth `ratio`, capped at twice dx), prism_z layers at the wall and
+    Kuhn tets above (wall_layout; n_prism overrides the count), farfield on x-in, x-out and top.
+    96x64x64 -> 42 prism layers, height 0.374, 1,327,104 cells."""
     xs = np.linspace(0.0, 1.0, nx + 1)
     ys = np.arange(ny + 1) * (1.0 / nx)
-    zs = _graded(nz, first, ratio)
+    zs, npz = wall_layout(nx, nz, first, ratio)
+    n_prism = npz if n_prism is None else n_prism
     return box_mesh(nx, ny, nz, layered_split(n_prism), xs=xs, ys=ys, zs=zs,
                     periodic=(False, True, False),
                     bc=dict(xmin=BC_FARFIELD, xmax=BC_FARFIELD, zmin=BC_NOSLIP, zmax=BC_FARFIELD),
                     jitter=jitter, seed=seed,
                     jitter_mask=(lambda i, j, k: k > n_prism) if jitter > 0 else None)
+
+
+def prism_slab(nx=32, ny=4, nz=24, first=1e-3, ratio=1.2, periodic=False):
+    """All-prism boundary-layer slab: x in [0,1], y periodic with dy = dx, z graded from the wall
+    (no-slip, farfield elsewhere) or periodic in every direction.  At 32x4x24 its level-2
+    agglomerates include one wrapping around its neighbour (a coarse face of zero net area)."""
+    z = _graded(nz, first, ratio)
+    bc = None if periodic else dict(xmin=BC_FARFIELD, xmax=BC_FARFIELD, zmin=BC_NOSLIP, zmax=BC_FARFIELD)
+    return box_mesh(nx, ny, nz, layered_split(nz), xs=np.linspace(0.0, 1.0, nx + 1), ys=np.arange(ny + 1) / nx,
+                    zs=z, periodic=(True, True, True) if periodic else (False, True, False), bc=bc)
 
 
 def ramp_box(nx=256, ny=128, nz=128, n_prism=8, angle_deg=15.0, jitter=0.0, seed=2402):

@@ -17,7 +17,7 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = ["orc_linalg.c", "orc_mesh.c", "orc_gks.c", "orc_solver.c", "orc_agglo.c", "orc_api.c"]
+_SRCS = ["orc_linalg.c", "orc_mesh.c", "orc_gks.c", "orc_solver.c", "orc_agglo.c", "orc_lusgs.c", "orc_api.c"]
 _LIB = os.path.join(_HERE, "liborc.so")
 _lib = None
 
@@ -42,7 +42,8 @@ class Params(C.Structure):
                 ("weno_eps", C.c_double), ("skew_min", C.c_double),
                 ("n_levels", C.c_int32), ("pre", C.c_int32), ("post", C.c_int32),
                 ("coarse_steps", C.c_int32), ("passes_per_level", C.c_int32), ("viscous", C.c_int32),
-                ("dt_mode", C.c_int32), ("precision", C.c_int32), ("agglo_seed", C.c_uint64)]
+                ("dt_mode", C.c_int32), ("precision", C.c_int32), ("coarse_smoother", C.c_int32),
+                ("agglo_seed", C.c_uint64)]
 
 
 def params(**kw) -> Params:
@@ -51,7 +52,7 @@ def params(**kw) -> Params:
     d = dict(gamma=1.4, mach=0.2, reynolds=1e4, prandtl=1.0, aoa=(0.0, 0.0), cfl_fine=0.5,
              cfl_coarse=0.5, eps_inviscid=0.01, c_press=1.0, weno_eps=1e-5, skew_min=0.2,
              n_levels=3, pre=1, post=0, coarse_steps=1, passes_per_level=2, viscous=0,
-             dt_mode=0, precision=0, agglo_seed=0)
+             dt_mode=0, precision=0, coarse_smoother=0, agglo_seed=0)
     d.update(kw)
     p = Params()
     for k, v in d.items():
@@ -92,6 +93,8 @@ def lib():
         _lib.orc_level_data.argtypes = [P, C.c_int, i32, d, d, i32, i32, i32, d, d]
         _lib.orc_kfvs_residual.argtypes = [P, C.c_int, d, d]
         _lib.orc_level_dt.argtypes = [P, C.c_int, d, d]
+        _lib.orc_colors.argtypes = [P, C.c_int, C.POINTER(C.c_int32)]
+        _lib.orc_lusgs.argtypes = [P, C.c_int, d, d, d, d, C.POINTER(C.c_int64)]
         _lib.orc_pt_moments.argtypes = [d, C.c_double, C.c_int, d]
         _lib.orc_pt_slope.argtypes = [d, C.c_double, d, d]
         _lib.orc_pt_time.argtypes = [C.c_double, C.c_double, C.c_double, d]
@@ -252,6 +255,25 @@ class Solver:
         if lib().orc_kfvs_residual(self.h, lev, _p(W, C.c_double), _p(R, C.c_double)):
             raise RuntimeError("oracle kfvs residual failed")
         return R
+
+    def colors(self, lev):
+        """(colour per cell, number of colours) of the LU-SGS ordering of level lev."""
+        n = self.level(lev)["nc"]
+        col = np.zeros(n, np.int32)
+        k = lib().orc_colors(self.h, lev, _p(col, C.c_int32))
+        if k < 0:
+            raise IndexError(lev)
+        return col, k
+
+    def lusgs(self, lev, W, rhs, dt):
+        """One LU-SGS step (Sec. 4.3) on level lev: (W + dU, cells skipped by positivity)."""
+        W, rhs, dt = _f64(W), _f64(rhs), _f64(dt)
+        out = np.zeros_like(W)
+        sk = C.c_int64()
+        if lib().orc_lusgs(self.h, lev, _p(W, C.c_double), _p(rhs, C.c_double), _p(dt, C.c_double),
+                           _p(out, C.c_double), C.byref(sk)):
+            raise RuntimeError("oracle LU-SGS step failed")
+        return out, sk.value
 
     def level_dt(self, lev, W):
         W = _f64(W)

@@ -19,6 +19,7 @@ typedef struct {
   double gamma, mach, reynolds, prandtl, aoa[2], cfl_fine, cfl_coarse, eps_inviscid, c_press,
       weno_eps, skew_min;
   int32_t n_levels, pre, post, coarse_steps, passes_per_level, viscous, dt_mode, precision;
+  int32_t coarse_smoother; /* 0 forward Euler, 1 LU-SGS (Sec. 4.3) */
   uint64_t agglo_seed;
 } orc_params;
 
@@ -83,6 +84,11 @@ double orc_cf_alpha(const orc_phys* ph, const double WL[5], const double WR[5], 
 int orc_bc_ghost(const orc_phys* ph, int tag, const double n[3], const double W[5], const double G[15],
                  double Wg[5], double Gg[15]);
 int orc_slope(const orc_maxw* g, double K, const double dW[5], double s[5]);
+
+/* implicit coarse smoother (orc_lusgs.c) */
+int orc_level_colors(const orc_level* L, int32_t* color);
+int orc_lusgs_step(const orc_params* P, const orc_level* L, const int32_t* color, int ncol, double* W,
+                   const double* RHS, const double* dt, int64_t* skipped);
 
 /* mesh (orc_mesh.c) */
 int orc_mesh_build(orc_mesh* M, int64_t n_nodes, const double* xyz, int64_t n_cells, const int8_t* ctype,

@@ -7,6 +7,7 @@
 
 typedef struct orc_solver orc_solver;
 orc_solver* orc_solver_new(orc_mesh* M, const orc_params* P, char* err);
+const orc_params* orc_solver_params(const orc_solver* S);
 void orc_solver_delete(orc_solver* S);
 int orc_solver_run(orc_solver* S, int multigrid, int n, double* hist);
 int orc_solver_reconstruct(orc_solver* S, double* rc, int mode);
@@ -177,6 +178,39 @@ int orc_level_data(void* hp, int lev, int32_t* map, double* vol, double* ctr, in
   if (Sn) memcpy(Sn, L->Sn, sizeof(double) * 3 * L->nf);
   if (area) memcpy(area, L->area, sizeof(double) * L->nf);
   return 0;
+}
+
+int orc_colors(void* hp, int lev, int32_t* colors) {
+  handle* h = hp;
+  if (lev < 0 || lev >= h->M->n_levels) return -1;
+  return orc_level_colors(&h->M->lev[lev], colors);
+}
+
+/* one LU-SGS step on level lev: Wout = W + dU for the defect RHS and time steps dt (SoA arrays) */
+int orc_lusgs(void* hp, int lev, const double* W, const double* RHS, const double* dt, double* Wout,
+              int64_t* skipped) {
+  handle* h = hp;
+  if (lev < 0 || lev >= h->M->n_levels) return -1;
+  const orc_level* L = &h->M->lev[lev];
+  int64_t n = L->nc;
+  double* w = malloc(sizeof(double) * 5 * n);
+  double* r = malloc(sizeof(double) * 5 * n);
+  int32_t* col = malloc(sizeof(int32_t) * n);
+  for (int64_t i = 0; i < n; ++i)
+    for (int q = 0; q < 5; ++q) {
+      w[5 * i + q] = W[q * n + i];
+      r[5 * i + q] = RHS[q * n + i];
+    }
+  int ncol = orc_level_colors(L, col);
+  *skipped = 0;
+  int rc = orc_lusgs_step(orc_solver_params(h->S), L, col, ncol, w, r, dt, skipped);
+  if (!rc)
+    for (int64_t i = 0; i < n; ++i)
+      for (int q = 0; q < 5; ++q) Wout[q * n + i] = w[5 * i + q];
+  free(w);
+  free(r);
+  free(col);
+  return rc;
 }
 
 int orc_kfvs_residual(void* hp, int lev, const double* W, double* res) {

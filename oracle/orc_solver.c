@@ -13,8 +13,8 @@
  *  - the residual restricted after the pre-smoothing step is a second fine residual evaluated at
  *    W^{n+1} (its gradient and compression-factor outputs are discarded);
  *  - the level-3 defect is the sum over level-2 cells of Res_2(W_2^{k}) + F_2 (FAS recursion);
- *  - only W is corrected on the fine level; a correction that would make rho or p non-positive in a
- *    cell is skipped for that cell;
+ *  - only W is corrected on the fine level; a correction or a coarse forward-Euler update that would
+ *    make rho or p non-positive in a cell is skipped for that cell (counted);
  *  - HWENO: sigma = |beta~_2 - beta~_1| (the printed beta~_0 does not exist), beta_2 from p^2,
  *    beta_1 = min(beta_GG of the alpha-scaled Green-Gauss p^1, beta_LS of the unweighted
  *    least-squares gradient), Omega = |Omega_0|, reconstruction of conservative variables;
@@ -36,6 +36,8 @@ typedef struct orc_solver {
   double r1;             /* first residual norm of the run */
   int64_t iters;
   int64_t skipped_corrections;
+  int32_t* colors[8]; /* LU-SGS cell colours per level (computed on first use) */
+  int ncolors[8];
 } orc_solver;
 
 int orc_build_levels(orc_mesh* M, const orc_params* P, char* err);
@@ -335,8 +337,10 @@ static void local_dt_level(const orc_solver* S, const orc_level* L, const double
       int32_t f = L->c2f[k];
       const double* Sn = L->Sn + 3 * f;
       double nn = sqrt(Sn[0] * Sn[0] + Sn[1] * Sn[1] + Sn[2] * Sn[2]);
-      double un = fabs((u[0] * Sn[0] + u[1] * Sn[1] + u[2] * Sn[2]) / nn);
-      sum += nn * (un + c);
+      /* the face's area is the sum of its fine faces' areas; its direction that of the summed
+         area vector (none when that vector cancels) */
+      double un = nn > 0.0 ? fabs((u[0] * Sn[0] + u[1] * Sn[1] + u[2] * Sn[2]) / nn) : 0.0;
+      sum += L->area[f] * (un + c);
     }
     dt[i] = S->P.cfl_coarse * L->vol[i] / sum;
   }
@@ -474,6 +478,9 @@ int orc_residual_kfvs(orc_solver* S, int lev, const double* W, double* Res) {
   for (int64_t f = 0; f < L->nf; ++f) {
     const double* Sn = L->Sn + 3 * f;
     double s = sqrt(Sn[0] * Sn[0] + Sn[1] * Sn[1] + Sn[2] * Sn[2]);
+    /* an agglomerate wrapping around its neighbour can leave a coarse face whose summed area
+       vector is exactly zero: no net area, no flux, and no normal to evaluate one with */
+    if (s == 0.0) continue;
     double n[3] = {Sn[0] / s, Sn[1] / s, Sn[2] / s}, F[5], Wg[5];
     int32_t a = L->fL[f], b = L->fR[f];
     if (b >= 0) {
@@ -503,6 +510,38 @@ static int physical(const double w[5], double g) {
   if (!(w[0] > 0.0)) return 0;
   double p = (g - 1.0) * (w[4] - 0.5 * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]) / w[0]);
   return p > 0.0;
+}
+
+/* coarse forward-Euler update W += dt/V (R + F); like the correction, an update that would make rho
+   or p non-positive in a cell is skipped for that cell (counted) */
+static int coarse_update(orc_solver* S, const orc_level* L, double* Wk, const double* R, const double* F,
+                         const double* dt) {
+  for (int64_t i = 0; i < L->nc; ++i) {
+    double w[5];
+    for (int q = 0; q < 5; ++q) w[q] = Wk[5 * i + q] + dt[i] / L->vol[i] * (R[5 * i + q] + F[5 * i + q]);
+    for (int q = 0; q < 5; ++q)
+      if (!isfinite(w[q])) return -1;
+    if (physical(w, S->P.gamma))
+      memcpy(Wk + 5 * i, w, sizeof(w));
+    else
+      S->skipped_corrections++;
+  }
+  return 0;
+}
+
+/* one coarse smoothing step on level l: forward Euler, or LU-SGS on the defect R + F (Sec. 4.3) */
+static int coarse_smooth(orc_solver* S, int l, double* Wk, const double* R, const double* F, const double* dt) {
+  const orc_level* L = &S->M->lev[l];
+  if (S->P.coarse_smoother != 1) return coarse_update(S, L, Wk, R, F, dt);
+  if (!S->colors[l]) {
+    S->colors[l] = malloc(sizeof(int32_t) * (L->nc ? L->nc : 1));
+    S->ncolors[l] = orc_level_colors(L, S->colors[l]);
+  }
+  double* rhs = malloc(sizeof(double) * 5 * (L->nc ? L->nc : 1));
+  for (int64_t j = 0; j < 5 * L->nc; ++j) rhs[j] = R[j] + F[j];
+  int rc = orc_lusgs_step(&S->P, L, S->colors[l], S->ncolors[l], Wk, rhs, dt, &S->skipped_corrections);
+  free(rhs);
+  return rc;
 }
 
 /* one explicit fine step (the fine-level smoother, Eq. smo) */
@@ -548,8 +587,7 @@ static int coarse_cycle(orc_solver* S, int l, double* Wk, const double* Rstar) {
   for (int s = 0; s < S->P.coarse_steps; ++s) {
     if ((rc = orc_residual_kfvs(S, l, Wk, R))) goto out;
     local_dt_level(S, L, Wk, dt);
-    for (int64_t i = 0; i < n; ++i)
-      for (int q = 0; q < 5; ++q) Wk[5 * i + q] += dt[i] / L->vol[i] * (R[5 * i + q] + F[5 * i + q]);
+    if ((rc = coarse_smooth(S, l, Wk, R, F, dt))) goto out;
   }
   if (l + 1 < S->M->n_levels) {
     const orc_level* C = &S->M->lev[l + 1];
@@ -591,8 +629,7 @@ static int coarse_cycle(orc_solver* S, int l, double* Wk, const double* Rstar) {
     for (int s = 0; s < S->P.post; ++s) {
       if ((rc = orc_residual_kfvs(S, l, Wk, R))) goto out;
       local_dt_level(S, L, Wk, dt);
-      for (int64_t i = 0; i < n; ++i)
-        for (int q = 0; q < 5; ++q) Wk[5 * i + q] += dt[i] / L->vol[i] * (R[5 * i + q] + F[5 * i + q]);
+      if ((rc = coarse_smooth(S, l, Wk, R, F, dt))) goto out;
     }
   }
 out:
@@ -687,11 +724,14 @@ orc_solver* orc_solver_new(orc_mesh* M, const orc_params* P, char* err) {
   return S;
 }
 
+const orc_params* orc_solver_params(const orc_solver* S) { return &S->P; }
+
 void orc_solver_delete(orc_solver* S) {
   if (!S) return;
   free(S->W);
   free(S->G);
   free(S->alpha);
+  for (int l = 0; l < 8; ++l) free(S->colors[l]);
   free(S);
 }
 

@@ -24,7 +24,7 @@ STATUS = {0: "CGKS_OK", 1: "CGKS_EINVAL", 2: "CGKS_ENOMEM", 3: "CGKS_ECUDA", 4: 
 EXPORTS = ["cgks_default_params", "cgks_create", "cgks_destroy", "cgks_set_params", "cgks_mesh_upload",
            "cgks_level_info", "cgks_coarse_map", "cgks_level_geometry", "cgks_fine_moments", "cgks_state_init",
            "cgks_state_get", "cgks_residual", "cgks_kfvs_residual", "cgks_kfvs_jvp", "cgks_step", "cgks_vcycle", "cgks_steady_solve",
-           "cgks_adjoint", "cgks_fp64_peak", "cgks_profile", "cgks_kernel_stats", "cgks_density_norm_noalloc",
+           "cgks_coarse_colors", "cgks_skipped_updates", "cgks_adjoint", "cgks_fp64_peak", "cgks_profile", "cgks_kernel_stats", "cgks_density_norm_noalloc",
            "cgks_last_error"]
 
 
@@ -40,7 +40,8 @@ class Params(C.Structure):
                 ("eps_inviscid", C.c_double), ("c_press", C.c_double), ("weno_eps", C.c_double),
                 ("skew_min", C.c_double), ("n_levels", C.c_int32), ("pre", C.c_int32), ("post", C.c_int32),
                 ("coarse_steps", C.c_int32), ("passes_per_level", C.c_int32), ("viscous", C.c_int32),
-                ("dt_mode", C.c_int32), ("precision", C.c_int32), ("agglo_seed", C.c_uint64)]
+                ("dt_mode", C.c_int32), ("precision", C.c_int32), ("coarse_smoother", C.c_int32),
+                ("agglo_seed", C.c_uint64)]
 
 
 def load(path: str = LIB_PATH):
@@ -70,6 +71,8 @@ def load(path: str = LIB_PATH):
             "cgks_vcycle": [P, C.c_int, C.POINTER(C.c_double)],
             "cgks_steady_solve": [P, C.c_int, C.c_double, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_double),
                                   C.POINTER(C.c_double)],
+            "cgks_coarse_colors": [P, C.c_int, i32, C.POINTER(C.c_int32)],
+            "cgks_skipped_updates": [P, C.POINTER(C.c_int64)],
             "cgks_adjoint": [P, d, C.c_int, d, d],
             "cgks_fp64_peak": [C.POINTER(C.c_double)],
             "cgks_profile": [P, C.c_int],
@@ -228,6 +231,20 @@ class Context:
         h = np.zeros(max(n, 1))
         _check(load().cgks_vcycle(self.h, n, h.ctypes.data_as(C.POINTER(C.c_double)) if history else None), self.h)
         return h[:n]
+
+    def coarse_colors(self, level):
+        """(colour per cell, number of colours) of the LU-SGS sweep order of a coarse level."""
+        n = self.level_info(level)[0]
+        col = self._empty(n, dtype=self.torch.int32)
+        k = C.c_int32()
+        _check(load().cgks_coarse_colors(self.h, level, _ptr(col), C.byref(k)), self.h)
+        return col, k.value
+
+    def skipped_updates(self):
+        """Cell updates skipped by the positivity rule since the last state_init."""
+        n = C.c_int64()
+        _check(load().cgks_skipped_updates(self.h, C.byref(n)), self.h)
+        return n.value
 
     def profile(self, enable=True):
         _check(load().cgks_profile(self.h, int(bool(enable))), self.h)

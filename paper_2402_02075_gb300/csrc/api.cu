@@ -251,6 +251,8 @@ static cgks_status check_params(cgks_ctx* ctx, const cgks_params* p) {
   if (p->n_levels < 1 || p->n_levels > 8 || p->passes_per_level < 0 || p->coarse_steps < 0 || p->pre < 0 || p->post < 0)
     return cgks_fail(ctx, CGKS_EINVAL, "multigrid counts out of range");
   if (p->precision != 0 && p->precision != 1) return cgks_fail(ctx, CGKS_EINVAL, "precision must be 0 or 1");
+  if (p->coarse_smoother != 0 && p->coarse_smoother != 1)
+    return cgks_fail(ctx, CGKS_EINVAL, "coarse_smoother must be 0 or 1");
   return CGKS_OK;
 }
 
@@ -277,6 +279,7 @@ cgks_status cgks_create(const cgks_params* params, void* cuda_stream, cgks_ctx**
   }
   if ((s = dalloc(ctx, ctx->ctx_allocs, &ctx->derr, 1)) != CGKS_OK ||
       (s = dalloc(ctx, ctx->ctx_allocs, &ctx->d_count, 1)) != CGKS_OK ||
+      (s = dalloc(ctx, ctx->ctx_allocs, &ctx->d_skipped, 1)) != CGKS_OK ||
       (s = dalloc(ctx, ctx->ctx_allocs, &ctx->nrm_part, 1024)) != CGKS_OK ||
       (s = dalloc(ctx, ctx->ctx_allocs, &ctx->nrm, 1)) != CGKS_OK) {
     g_create_error = ctx->err;
@@ -422,6 +425,7 @@ cgks_status cgks_state_init(cgks_ctx* ctx, const double* W, const double* gradW,
     CK(cudaMemcpyAsync(ctx->alpha, alpha, sizeof(double) * n, cudaMemcpyDefault, st));
   else
     k_fill<<<grid_for(n, 256), 256, 0, st>>>(n, 1.0, ctx->alpha);
+  CK(cudaMemsetAsync(ctx->d_skipped, 0, sizeof(int64_t), st));
   CK(cudaGetLastError());
   ctx->has_state = true;
   ctx->iters = 0;
@@ -543,6 +547,21 @@ cgks_status cgks_steady_solve(cgks_ctx* ctx, int multigrid, double drop, int64_t
   if (final_drop) *final_drop = ratio;
   if (seconds) *seconds = sec;
   if (ratio > drop) return cgks_fail(ctx, CGKS_ENOTCONV, "steady solve: max_iters reached before the drop");
+  return CGKS_OK;
+}
+
+cgks_status cgks_coarse_colors(cgks_ctx* ctx, int level, int32_t* colors, int32_t* n_colors) {
+  NEED_MESH();
+  if (level < 1 || level >= (int)ctx->L.size()) return cgks_fail(ctx, CGKS_EINVAL, "cgks_coarse_colors: bad level");
+  return lusgs_color_count(ctx, level, colors, n_colors);
+}
+
+cgks_status cgks_skipped_updates(cgks_ctx* ctx, int64_t* count) {
+  NEED_STATE();
+  if (!count) return cgks_fail(ctx, CGKS_EINVAL, "count is NULL");
+  CK(cudaMemcpyAsync(ctx->h_count, ctx->d_skipped, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  *count = *ctx->h_count;
   return CGKS_OK;
 }
 

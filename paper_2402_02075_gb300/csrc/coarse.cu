@@ -13,6 +13,11 @@ __global__ void k_kfvs_faces(int64_t nf, const int32_t* __restrict__ fL, const i
   if (f >= nf) return;
   const double S[3] = {Sn[f], Sn[nf + f], Sn[2 * nf + f]};
   const double s = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+  if (s == 0.0) {  // a coarse face whose summed area vectors cancel carries no flux
+#pragma unroll
+    for (int q = 0; q < 5; ++q) ff[q * nf + f] = 0.0;
+    return;
+  }
   const double n[3] = {S[0] / s, S[1] / s, S[2] / s};
   const int64_t L = fL[f], R = fR[f];
   double WL[5], WR[5], F[5];
@@ -41,6 +46,11 @@ __global__ void k_kfvs_jvp_faces(int64_t nf, const int32_t* __restrict__ fL, con
   if (f >= nf) return;
   const float S[3] = {float(Sn[f]), float(Sn[nf + f]), float(Sn[2 * nf + f])};
   const float s = sqrtf(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+  if (s == 0.0f) {  // no net area, no flux
+#pragma unroll
+    for (int q = 0; q < 5; ++q) ff[q * nf + f] = 0.0f;
+    return;
+  }
   const D n[3] = {D(S[0] / s), D(S[1] / s), D(S[2] / s)};
   const int64_t L = fL[f], R = fR[f];
   D WL[5], WR[5], F[5];
@@ -83,8 +93,12 @@ __global__ void k_kfvs_gather(int64_t nc, int64_t nf, const int32_t* __restrict_
   for (int q = 0; q < 5; ++q) res[q * nc + c] = r[q];
 }
 
+// local time step CFL |Omega| / sum_p A_p (|u . n_p| + c): A_p the area of the coarse face (the sum
+// of its fine faces' areas), n_p the direction of its summed area vector (no |u . n| term when that
+// vector cancels)
 __global__ void k_coarse_dt(int64_t nc, int64_t nf, const int32_t* __restrict__ ptr, const int32_t* __restrict__ c2f,
-                            const double* __restrict__ Sn, const double* __restrict__ vol, const double* __restrict__ W,
+                            const double* __restrict__ Sn, const double* __restrict__ area,
+                            const double* __restrict__ vol, const double* __restrict__ W,
                             double* __restrict__ dt, double gamma, double cfl) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= nc) return;
@@ -97,7 +111,8 @@ __global__ void k_coarse_dt(int64_t nc, int64_t nf, const int32_t* __restrict__ 
     const int64_t f = c2f[k];
     const double S[3] = {Sn[f], Sn[nf + f], Sn[2 * nf + f]};
     const double a = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
-    s += fabs(u[0] * S[0] + u[1] * S[1] + u[2] * S[2]) + a * snd;
+    const double un = a > 0.0 ? fabs(u[0] * S[0] + u[1] * S[1] + u[2] * S[2]) / a : 0.0;
+    s += area[f] * (un + snd);
   }
   dt[c] = cfl * vol[c] / s;
 }
@@ -108,21 +123,26 @@ __global__ void k_forcing(int64_t n5, const double* __restrict__ Rs, const doubl
   if (j < n5) F[j] = Rs[j] - R[j];
 }
 
-// W += dt / V (R + F)
+// W += dt / V (R + F); an update that would make rho or p non-positive is skipped for that cell
+// (counted), a non-finite one is an error
 __global__ void k_fe_update(int64_t nc, const double* __restrict__ dt, const double* __restrict__ vol,
                             const double* __restrict__ R, const double* __restrict__ F, double* __restrict__ W,
-                            double gamma, DevErr* err) {
+                            double gamma, unsigned long long* skipped, DevErr* err) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= nc) return;
   const double h = dt[c] / vol[c];
   double w[5];
 #pragma unroll
-  for (int q = 0; q < 5; ++q) {
-    w[q] = W[q * nc + c] + h * (R[q * nc + c] + F[q * nc + c]);
-    W[q * nc + c] = w[q];
-  }
+  for (int q = 0; q < 5; ++q) w[q] = W[q * nc + c] + h * (R[q * nc + c] + F[q * nc + c]);
   const double p = (gamma - 1.0) * (w[4] - 0.5 * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]) / w[0]);
-  if (!(w[0] > 0.0) || !(p > 0.0) || !isfinite(p)) set_err(err, CGKS_ENAN, (int)c, 22);
+  if (!(isfinite(w[0]) && isfinite(w[1]) && isfinite(w[2]) && isfinite(w[3]) && isfinite(w[4]))) {
+    set_err(err, CGKS_ENAN, (int)c, 22);
+  } else if (w[0] > 0.0 && p > 0.0) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) W[q * nc + c] = w[q];
+  } else {
+    atomicAdd(skipped, 1ULL);
+  }
 }
 
 // coarse state = sum V_i W_i / V_c and coarse defect = sum (R_i [+ F_i]) over the finer cells of
@@ -229,7 +249,7 @@ cgks_status kfvs_jvp(cgks_ctx* ctx, int lev, const double* W0, const double* X, 
 
 cgks_status coarse_dt(cgks_ctx* ctx, int lev, const double* W, double* dt) {
   const Level& L = ctx->L[lev];
-  k_coarse_dt<<<grid_for(L.nc, 256), 256, 0, ctx->stream>>>(L.nc, L.nf, L.c2f_ptr, L.c2f, L.Sn, L.vol, W, dt,
+  k_coarse_dt<<<grid_for(L.nc, 256), 256, 0, ctx->stream>>>(L.nc, L.nf, L.c2f_ptr, L.c2f, L.Sn, L.area, L.vol, W, dt,
                                                             ctx->P.gamma, ctx->P.cfl_coarse);
   if (ctx->P.dt_mode == 1) CKS(global_min_dt(ctx, dt, L.nc));
   CK(cudaGetLastError());
@@ -252,8 +272,9 @@ static cgks_status coarse_smooth(cgks_ctx* ctx, int l) {
   const Level& L = ctx->L[l];
   CoarseBuf& B = ctx->C[l];
   CKS(coarse_dt(ctx, l, B.W, B.dt));
+  if (ctx->P.coarse_smoother == 1) return lusgs_step(ctx, l);
   k_fe_update<<<grid_for(L.nc, 256), 256, 0, ctx->stream>>>(L.nc, B.dt, L.vol, B.R, B.F, B.W, ctx->P.gamma,
-                                                             ctx->derr);
+                                                             (unsigned long long*)ctx->d_skipped, ctx->derr);
   CK(cudaGetLastError());
   return CGKS_OK;
 }
@@ -286,7 +307,7 @@ static cgks_status coarse_cycle(cgks_ctx* ctx, int l) {
     CK(cudaMemcpyAsync(N.W0, N.W, sizeof(double) * 5 * Cn.nc, cudaMemcpyDeviceToDevice, st));
     CKS(coarse_cycle(ctx, l + 1));
     k_prolong<<<grid_for(L.nc, 256), 256, 0, st>>>(L.nc, Cn.nc, Cn.f2c, N.W, N.W0, B.W, ctx->P.gamma,
-                                                   (unsigned long long*)ctx->d_count);
+                                                   (unsigned long long*)ctx->d_skipped);
     for (int s = 0; s < ctx->P.post; ++s) {
       CKS(coarse_residual(ctx, l));
       CKS(coarse_smooth(ctx, l));
@@ -322,7 +343,7 @@ cgks_status vcycle_once(cgks_ctx* ctx, double* norm_dev) {
   CK(cudaMemcpyAsync(B1.W0, B1.W, sizeof(double) * 5 * C1.nc, cudaMemcpyDeviceToDevice, st));
   CKS(coarse_cycle(ctx, 1));
   k_prolong<<<grid_for(F.nc, 256), 256, 0, st>>>(F.nc, C1.nc, C1.f2c, B1.W, B1.W0, ctx->W, ctx->P.gamma,
-                                                 (unsigned long long*)ctx->d_count);
+                                                 (unsigned long long*)ctx->d_skipped);
   for (int s = 0; s < ctx->P.post; ++s) CKS(step_once(ctx, nullptr));
   CK(cudaGetLastError());
   return CGKS_OK;

@@ -74,6 +74,11 @@ struct Fine {
 struct CoarseBuf {  // per coarse level work arrays
   double *W = nullptr, *W0 = nullptr, *Rs = nullptr, *F = nullptr, *R = nullptr, *dt = nullptr, *ff = nullptr;
   float* ff32 = nullptr;  // FP32 directional derivatives of the face fluxes (precision 1)
+  // LU-SGS smoother (coarse_smoother 1): colours, colour-major cell order and its offsets,
+  // per-face lambda, diagonal, increments
+  int32_t *color = nullptr, *order = nullptr;
+  std::vector<int64_t> coff;
+  double *lam = nullptr, *Dg = nullptr, *dU = nullptr;
 };
 
 struct cgks_ctx {
@@ -97,6 +102,7 @@ struct cgks_ctx {
   DevErr* h_err = nullptr;
   int64_t* d_count = nullptr;
   int64_t* h_count = nullptr;
+  int64_t* d_skipped = nullptr;     // coarse updates and corrections skipped by the positivity rule
   double r1 = 0.0;
   int64_t iters = 0;
   std::vector<void*> mesh_allocs;   // freed on re-upload / destroy
@@ -166,4 +172,7 @@ cgks_status kfvs_residual(cgks_ctx* ctx, int lev, const double* W, double* res);
 cgks_status kfvs_jvp(cgks_ctx* ctx, int lev, const double* W0, const double* X, int x_is_state, double* res);
 cgks_status coarse_dt(cgks_ctx* ctx, int lev, const double* W, double* dt);
 cgks_status vcycle_once(cgks_ctx* ctx, double* norm_dev);
+// LU-SGS step on coarse level l for the defect C[l].R + C[l].F with the time steps in C[l].dt
+cgks_status lusgs_step(cgks_ctx* ctx, int l);
+cgks_status lusgs_color_count(cgks_ctx* ctx, int l, int32_t* colors, int32_t* n_colors);
 cgks_status step_once(cgks_ctx* ctx, double* norm_dev);

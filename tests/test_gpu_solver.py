@@ -86,7 +86,7 @@ def test_coarsening_is_bit_exact(cg, orc, name, mk, seed):
 
 
 @pytest.mark.parametrize("mk", [lambda: mg.periodic_box(8), lambda: mg.wall_box(16, 8, 16, n_prism=6),
-                                lambda: mg.ramp_box(24, 12, 8, n_prism=3)])
+                                lambda: mg.ramp_box(24, 12, 8, n_prism=3), lambda: mg.prism_slab()])
 def test_coarse_kfvs_residuals(cg, orc, mk):
     mesh = mk()
     prm = dict(n_levels=3, mach=0.6)
@@ -103,7 +103,7 @@ def test_coarse_kfvs_residuals(cg, orc, mk):
         assert_normwise(got, ref, 1e-12, f"KFVS residual level {lev}")
 
 
-@pytest.mark.parametrize("case", ["wave", "wall", "ramp"])
+@pytest.mark.parametrize("case", ["wave", "wall", "ramp", "slab"])
 def test_vcycles(cg, orc, case):
     rng = np.random.default_rng(11)
     if case == "wave":
@@ -116,16 +116,22 @@ def test_vcycles(cg, orc, case):
         W, G = mg.uniform_state(len(mesh["cell_type"]), mach=0.5)
         prm = dict(mach=0.5, viscous=1, reynolds=1e4, prandtl=0.72)
         n = 3
-    else:
+    elif case == "ramp":
         mesh = mg.ramp_box(24, 12, 8, n_prism=3)
         W, G = mg.uniform_state(len(mesh["cell_type"]), mach=3.0)
         prm = dict(mach=3.0)
+        n = 3
+    else:  # a level-2 coarse face of zero net area
+        mesh = mg.prism_slab()
+        W, G = mg.uniform_state(len(mesh["cell_type"]), mach=0.5)
+        prm = dict(mach=0.5, viscous=1, reynolds=1e4, prandtl=0.72)
         n = 3
     ctx, om, os_ = _pair(cg, orc, mesh, W, G, n_levels=3, **prm)
     hg = ctx.vcycle(n)
     ho = os_.run(n, multigrid=True)
     np.testing.assert_allclose(hg, ho, rtol=1e-9)
     _compare_states(ctx, os_)
+    assert ctx.skipped_updates() == os_.skipped()
 
 
 def test_runs_are_bitwise_reproducible(cg):
@@ -174,3 +180,41 @@ def test_error_paths(cg):
     assert e.value.status == 5 and "index" in str(e.value)
     assert cg.load().cgks_adjoint(ctx.h, None, 0, None, None) == 8
     ctx.close()
+
+
+@pytest.mark.parametrize("mk", [lambda: mg.periodic_box(8), lambda: mg.wall_box(16, 8, 16, n_prism=6),
+                                lambda: mg.prism_slab()])
+def test_lusgs_colours_are_bit_exact(cg, orc, mk):
+    mesh = mk()
+    ctx = cg.upload_mesh(mesh, cg.default_params(n_levels=3, coarse_smoother=1))
+    S = orc.Solver(orc.Mesh(mesh), orc.params(n_levels=3, coarse_smoother=1))
+    for lev in (1, 2):
+        col, k = ctx.coarse_colors(lev)
+        ref, kr = S.colors(lev)
+        assert k == kr
+        assert np.array_equal(col.cpu().numpy(), ref)
+    ctx.close()
+
+
+@pytest.mark.parametrize("case", ["wave", "wall", "ramp"])
+def test_vcycles_with_lusgs_coarse_smoother(cg, orc, case):
+    """V-cycles whose coarse levels relax with LU-SGS (Sec. 4.3) against the oracle: the colour-major
+    parallel sweep equals the oracle's sequential sweep in (colour, id) order."""
+    if case == "wave":
+        mesh = mg.periodic_box(8)
+        W, G = mg.density_wave_state(mesh)
+        prm = dict(mach=0.2)
+    elif case == "wall":
+        mesh = mg.wall_box(16, 8, 16, n_prism=6)
+        W, G = mg.uniform_state(len(mesh["cell_type"]), mach=0.5)
+        prm = dict(mach=0.5, viscous=1, reynolds=1e4, prandtl=0.72)
+    else:
+        mesh = mg.ramp_box(24, 12, 8, n_prism=3)
+        W, G = mg.uniform_state(len(mesh["cell_type"]), mach=3.0)
+        prm = dict(mach=3.0)
+    ctx, om, os_ = _pair(cg, orc, mesh, W, G, n_levels=3, coarse_smoother=1, **prm)
+    hg = ctx.vcycle(3)
+    ho = os_.run(3, multigrid=True)
+    np.testing.assert_allclose(hg, ho, rtol=1e-9)
+    _compare_states(ctx, os_)
+    assert ctx.skipped_updates() == os_.skipped()

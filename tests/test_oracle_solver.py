@@ -142,3 +142,27 @@ def test_design_order_on_smooth_density_wave(orc):
     e2 = _wave_error(orc, 32, 0.2)
     assert e1 < 2e-5
     assert np.log2(e1 / e2) > 2.2
+
+
+def test_zero_area_coarse_face_carries_no_flux(orc):
+    """A coarse face with zero net area vector contributes nothing (it has no normal); the KFVS
+    residual stays finite, keeps the free stream and telescopes, and V-cycles conserve mass, momentum
+    and energy on that hierarchy."""
+    M, S, W = _uniform(orc, mg.prism_slab(periodic=True), mach=0.5, n_levels=3, dt_mode=1)
+    L = S.level(2)
+    area = np.linalg.norm(L["Sn"], axis=1)
+    assert (area == 0.0).sum() == 1
+    Wl = np.repeat(W[:, :1], L["nc"], axis=1)
+    assert np.abs(S.kfvs_residual(2, Wl)).max() < 1e-13 * area.max()
+    rng = np.random.default_rng(2)
+    Wp = Wl * (1.0 + 0.01 * rng.normal(size=Wl.shape))
+    R = S.kfvs_residual(2, Wp)
+    assert np.isfinite(R).all()
+    assert np.all(np.abs(R.sum(axis=1)) < 1e-14 * np.abs(R).sum(axis=1).max())
+    # a perturbed fine state through two V-cycles: totals conserved (dt_mode 1, periodic)
+    vol, _, _ = M.cells()
+    Wf = W * (1.0 + 0.01 * rng.normal(size=W.shape))
+    S.set_state(Wf, np.zeros((15, M.nc)))
+    before = Wf @ vol
+    S.run(2, multigrid=True)
+    np.testing.assert_allclose(S.state()[0] @ vol, before, rtol=1e-13, atol=1e-15)
