@@ -42,10 +42,10 @@ SAMPLE = dict(nx=96, ny=4, nz=64)
 # FP64 floating-point operations per Gauss point of the gas-kinetic flux kernel (2 per DFMA, 1 per
 # DADD/DMUL), from the ncu instruction counts of a full capture of the kernel on the 48x32x32 box;
 # the kernel's own arithmetic, all of which the method needs
-FLOP_PER_GP = 3418.9
+FLOP_PER_GP = 3422.8
 # DRAM bytes (read + write) per Gauss point of the same kernel from the same capture (None when the
 # kernel has changed since)
-DRAM_BYTES_PER_GP = 191.5
+DRAM_BYTES_PER_GP = 160.7
 
 
 def workload_name(w):
