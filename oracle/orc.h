@@ -17,7 +17,7 @@
 
 typedef struct {
   double gamma, mach, reynolds, prandtl, aoa[2], cfl_fine, cfl_coarse, eps_inviscid, c_press,
-      weno_eps, skew_min;
+      weno_eps, skew_min, correction_relax;
   int32_t n_levels, pre, post, coarse_steps, passes_per_level, viscous, dt_mode, precision;
   int32_t coarse_smoother; /* 0 forward Euler, 1 LU-SGS (Sec. 4.3) */
   uint64_t agglo_seed;

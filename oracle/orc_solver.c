@@ -616,7 +616,7 @@ static int coarse_cycle(orc_solver* S, int l, double* Wk, const double* Rstar) {
       for (int64_t i = 0; i < n; ++i) {
         int32_t c = C->fine2coarse[i];
         double w[5];
-        for (int q = 0; q < 5; ++q) w[q] = Wk[5 * i + q] + (Wc[5 * c + q] - Wc0[5 * c + q]);
+        for (int q = 0; q < 5; ++q) w[q] = Wk[5 * i + q] + S->P.correction_relax * (Wc[5 * c + q] - Wc0[5 * c + q]);
         if (physical(w, S->P.gamma))
           memcpy(Wk + 5 * i, w, sizeof(w));
         else
@@ -673,7 +673,7 @@ static int vcycle(orc_solver* S, double* norm) {
   for (int64_t i = 0; i < nc; ++i) {
     int32_t c = C->fine2coarse[i];
     double w[5];
-    for (int q = 0; q < 5; ++q) w[q] = S->W[5 * i + q] + (Wc[5 * c + q] - Wc0[5 * c + q]);
+    for (int q = 0; q < 5; ++q) w[q] = S->W[5 * i + q] + S->P.correction_relax * (Wc[5 * c + q] - Wc0[5 * c + q]);
     if (physical(w, S->P.gamma))
       memcpy(S->W + 5 * i, w, sizeof(w));
     else

@@ -234,6 +234,7 @@ cgks_status cgks_default_params(cgks_params* p) {
   p->c_press = 1.0;
   p->weno_eps = 1e-5;
   p->skew_min = 0.2;
+  p->correction_relax = 1.0;
   p->n_levels = 3;
   p->pre = 1;
   p->post = 0;
@@ -251,6 +252,8 @@ static cgks_status check_params(cgks_ctx* ctx, const cgks_params* p) {
   if (p->n_levels < 1 || p->n_levels > 8 || p->passes_per_level < 0 || p->coarse_steps < 0 || p->pre < 0 || p->post < 0)
     return cgks_fail(ctx, CGKS_EINVAL, "multigrid counts out of range");
   if (p->precision != 0 && p->precision != 1) return cgks_fail(ctx, CGKS_EINVAL, "precision must be 0 or 1");
+  if (!(p->correction_relax > 0.0) || !(p->correction_relax <= 1.0))
+    return cgks_fail(ctx, CGKS_EINVAL, "correction_relax must be in (0, 1]");
   if (p->coarse_smoother != 0 && p->coarse_smoother != 1)
     return cgks_fail(ctx, CGKS_EINVAL, "coarse_smoother must be 0 or 1");
   return CGKS_OK;

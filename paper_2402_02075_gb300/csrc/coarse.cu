@@ -171,16 +171,17 @@ __global__ void k_restrict(int64_t ncc, int64_t ncf, const int32_t* __restrict__
   }
 }
 
-// W_f += W_c - W_c^0 (injection); a correction that would make rho or p non-positive is skipped
+// W_f += r (W_c - W_c^0) (injection, r = correction_relax); a correction that would make rho or p
+// non-positive is skipped
 __global__ void k_prolong(int64_t ncf, int64_t ncc, const int32_t* __restrict__ f2c, const double* __restrict__ Wc,
-                          const double* __restrict__ Wc0, double* __restrict__ Wf, double gamma,
+                          const double* __restrict__ Wc0, double* __restrict__ Wf, double gamma, double relax,
                           unsigned long long* skipped) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= ncf) return;
   const int64_t c = f2c[i];
   double w[5];
 #pragma unroll
-  for (int q = 0; q < 5; ++q) w[q] = Wf[q * ncf + i] + (Wc[q * ncc + c] - Wc0[q * ncc + c]);
+  for (int q = 0; q < 5; ++q) w[q] = Wf[q * ncf + i] + relax * (Wc[q * ncc + c] - Wc0[q * ncc + c]);
   const double p = (gamma - 1.0) * (w[4] - 0.5 * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]) / w[0]);
   if (w[0] > 0.0 && p > 0.0) {
 #pragma unroll
@@ -306,7 +307,7 @@ static cgks_status coarse_cycle(cgks_ctx* ctx, int l) {
                                                      N.W, N.Rs);
     CK(cudaMemcpyAsync(N.W0, N.W, sizeof(double) * 5 * Cn.nc, cudaMemcpyDeviceToDevice, st));
     CKS(coarse_cycle(ctx, l + 1));
-    k_prolong<<<grid_for(L.nc, 256), 256, 0, st>>>(L.nc, Cn.nc, Cn.f2c, N.W, N.W0, B.W, ctx->P.gamma,
+    k_prolong<<<grid_for(L.nc, 256), 256, 0, st>>>(L.nc, Cn.nc, Cn.f2c, N.W, N.W0, B.W, ctx->P.gamma, ctx->P.correction_relax,
                                                    (unsigned long long*)ctx->d_skipped);
     for (int s = 0; s < ctx->P.post; ++s) {
       CKS(coarse_residual(ctx, l));
@@ -342,7 +343,7 @@ cgks_status vcycle_once(cgks_ctx* ctx, double* norm_dev) {
                                                    nullptr, B1.W, B1.Rs);
   CK(cudaMemcpyAsync(B1.W0, B1.W, sizeof(double) * 5 * C1.nc, cudaMemcpyDeviceToDevice, st));
   CKS(coarse_cycle(ctx, 1));
-  k_prolong<<<grid_for(F.nc, 256), 256, 0, st>>>(F.nc, C1.nc, C1.f2c, B1.W, B1.W0, ctx->W, ctx->P.gamma,
+  k_prolong<<<grid_for(F.nc, 256), 256, 0, st>>>(F.nc, C1.nc, C1.f2c, B1.W, B1.W0, ctx->W, ctx->P.gamma, ctx->P.correction_relax,
                                                  (unsigned long long*)ctx->d_skipped);
   for (int s = 0; s < ctx->P.post; ++s) CKS(step_once(ctx, nullptr));
   CK(cudaGetLastError());

@@ -218,3 +218,16 @@ def test_vcycles_with_lusgs_coarse_smoother(cg, orc, case):
     np.testing.assert_allclose(hg, ho, rtol=1e-9)
     _compare_states(ctx, os_)
     assert ctx.skipped_updates() == os_.skipped()
+
+
+def test_vcycles_with_relaxed_correction(cg, orc):
+    """correction_relax r < 1 scales the injected coarse correction on every level, the same way in
+    the oracle."""
+    mesh = mg.wall_box(16, 8, 16, n_prism=6)
+    W, G = mg.uniform_state(len(mesh["cell_type"]), mach=0.5)
+    prm = dict(mach=0.5, viscous=1, reynolds=1e4, prandtl=0.72, correction_relax=0.5)
+    ctx, om, os_ = _pair(cg, orc, mesh, W, G, n_levels=3, **prm)
+    hg = ctx.vcycle(3)
+    ho = os_.run(3, multigrid=True)
+    np.testing.assert_allclose(hg, ho, rtol=1e-9)
+    _compare_states(ctx, os_)
