@@ -66,6 +66,9 @@ typedef struct {
                           correction, cgks_kfvs_jvp); the fine level, the defect, its restriction,
                           the states, updates and correction stay FP64 */
   int32_t coarse_smoother; /* 0 forward Euler (Sec. 4.2); 1 LU-SGS, the implicit variant of Sec. 4.3 */
+  int32_t prolongation;    /* 0 injection (Sec. 4.2); 1 injection smoothed once over face neighbours: a
+                              cell receives the volume-weighted mean of its own and its neighbours'
+                              injected corrections (not in the paper) */
   uint64_t agglo_seed; /* 0: the paper's hash on cell ids; s > 0 relabels cell N as splitmix64(N ^ s) >> 33 */
 } cgks_params;
 

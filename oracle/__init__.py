@@ -42,7 +42,7 @@ class Params(C.Structure):
                 ("weno_eps", C.c_double), ("skew_min", C.c_double), ("correction_relax", C.c_double),
                 ("n_levels", C.c_int32), ("pre", C.c_int32), ("post", C.c_int32),
                 ("coarse_steps", C.c_int32), ("passes_per_level", C.c_int32), ("viscous", C.c_int32),
-                ("dt_mode", C.c_int32), ("precision", C.c_int32), ("coarse_smoother", C.c_int32),
+                ("dt_mode", C.c_int32), ("precision", C.c_int32), ("coarse_smoother", C.c_int32), ("prolongation", C.c_int32),
                 ("agglo_seed", C.c_uint64)]
 
 
@@ -52,7 +52,7 @@ def params(**kw) -> Params:
     d = dict(gamma=1.4, mach=0.2, reynolds=1e4, prandtl=1.0, aoa=(0.0, 0.0), cfl_fine=0.5,
              cfl_coarse=0.5, eps_inviscid=0.01, c_press=1.0, weno_eps=1e-5, skew_min=0.2, correction_relax=1.0,
              n_levels=3, pre=1, post=0, coarse_steps=1, passes_per_level=2, viscous=0,
-             dt_mode=0, precision=0, coarse_smoother=0, agglo_seed=0)
+             dt_mode=0, precision=0, coarse_smoother=0, prolongation=0, agglo_seed=0)
     d.update(kw)
     p = Params()
     for k, v in d.items():
@@ -77,6 +77,7 @@ def lib():
         _lib.orc_mesh_delete.argtypes = [P]
         _lib.orc_mesh_counts.argtypes = [P, i64]
         _lib.orc_mesh_cells.argtypes = [P, d, d, d]
+        _lib.orc_mesh_coarsening_geometry.argtypes = [P, d, d, d, d]
         _lib.orc_mesh_faces.argtypes = [P, i32, i32, i32, i32, d, d, d, i32, C.POINTER(C.c_int8)]
         _lib.orc_mesh_qpoints.argtypes = [P, C.POINTER(C.c_int8), i64, i32, d, C.c_int, d, d]
         _lib.orc_new.restype = P
@@ -150,6 +151,15 @@ class Mesh:
         vol, ctr, m2 = np.zeros(self.nc), np.zeros((self.nc, 3)), np.zeros((self.nc, 6))
         lib().orc_mesh_cells(self.h, _p(vol, C.c_double), _p(ctr, C.c_double), _p(m2, C.c_double))
         return vol, ctr, m2
+
+    def coarsening_geometry(self):
+        """(vol, ctr [nc][3], Sn [nf][3], area) of the fine level as the coarsening sees it: node-mean
+        centres, area vectors from the diagonals, divergence-theorem volumes."""
+        vol, ctr = np.zeros(self.nc), np.zeros((self.nc, 3))
+        Sn, area = np.zeros((self.nf, 3)), np.zeros(self.nf)
+        lib().orc_mesh_coarsening_geometry(self.h, _p(vol, C.c_double), _p(ctr, C.c_double), _p(Sn, C.c_double),
+                                           _p(area, C.c_double))
+        return vol, ctr, Sn, area
 
     def faces(self):
         nf, nc = self.nf, self.nc

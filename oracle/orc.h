@@ -20,6 +20,7 @@ typedef struct {
       weno_eps, skew_min, correction_relax;
   int32_t n_levels, pre, post, coarse_steps, passes_per_level, viscous, dt_mode, precision;
   int32_t coarse_smoother; /* 0 forward Euler, 1 LU-SGS (Sec. 4.3) */
+  int32_t prolongation;    /* 0 injection, 1 injection smoothed over face neighbours */
   uint64_t agglo_seed;
 } orc_params;
 
@@ -42,6 +43,8 @@ typedef struct {
   int64_t n_nodes, nc, nf, n_int, n_per, n_bnd;
   int8_t *ctype;                 /* 4 tet, 5 prism, 6 hex (= number of faces) */
   double *vol, *ctr, *m2;        /* [nc], [nc][3], [nc][6] central second-moment averages xx,yy,zz,xy,yz,xz */
+  /* geometry of the coarsening (orc_mesh.c canon_face): [nc], [nc][3], [nf][3], [nf], [nf][3] */
+  double *cvol, *cctr, *cSn, *carea, *camom;
   int32_t *fL, *fR, *ftag, *ftagR, *fngp;
   double *shift;                 /* [nf][3] */
   double *gx, *gA;               /* [nf][4][3] Gauss points and area vectors dA_k (|dA_k| = weight) */

@@ -310,6 +310,13 @@ int orc_build_levels(orc_mesh* M, const orc_params* P, char* err) {
   for (int l = 1; l < nl; ++l) {
     orc_level cur, nxt;
     level_copy(&M->lev[l - 1], &cur);
+    if (l == 1) { /* level 1 is built from the coarsening's own geometry of the fine level */
+      memcpy(cur.vol, M->cvol, sizeof(double) * M->nc);
+      memcpy(cur.ctr, M->cctr, sizeof(double) * 3 * M->nc);
+      memcpy(cur.Sn, M->cSn, sizeof(double) * 3 * M->nf);
+      memcpy(cur.area, M->carea, sizeof(double) * M->nf);
+      memcpy(cur.amom, M->camom, sizeof(double) * 3 * M->nf);
+    }
     int32_t* comp = malloc(sizeof(int32_t) * cur.nc);
     for (int64_t i = 0; i < cur.nc; ++i) comp[i] = (int32_t)i;
     for (int p = 0; p < P->passes_per_level; ++p) {

@@ -61,6 +61,14 @@ void orc_mesh_cells(void* m, double* vol, double* ctr, double* m2) {
   memcpy(m2, M->m2, sizeof(double) * 6 * M->nc);
 }
 
+void orc_mesh_coarsening_geometry(void* m, double* vol, double* ctr, double* Sn, double* area) {
+  orc_mesh* M = m;
+  memcpy(vol, M->cvol, sizeof(double) * M->nc);
+  memcpy(ctr, M->cctr, sizeof(double) * 3 * M->nc);
+  memcpy(Sn, M->cSn, sizeof(double) * 3 * M->nf);
+  memcpy(area, M->carea, sizeof(double) * M->nf);
+}
+
 void orc_mesh_faces(void* m, int32_t* fL, int32_t* fR, int32_t* ftag, int32_t* fngp, double* gx, double* gA,
                     double* shift, int32_t* cf, int8_t* cside) {
   orc_mesh* M = m;

@@ -115,6 +115,29 @@ static void face_gp(const double* P, int nv, double* gx, double* gA) {
   }
 }
 
+/* Geometry of the coarsening.  The agglomeration compares a skewness measure with a limit, so its
+   inputs are defined by one formula with a fixed order of operations (this file is compiled without
+   floating-point contraction): a face of nodes P_0..P_{n-1} (its left cell's local order) has area
+   vector 1/2 (P_1 - P_0) x (P_2 - P_0) (triangle) or 1/2 (P_2 - P_0) x (P_3 - P_1) (quadrilateral,
+   exact for a bilinear face), centre the node mean and area the length of the area vector; a cell
+   has centre the node mean and volume 1/3 sum over its faces (own local order, outward) of
+   centre . area vector (the divergence theorem for flat faces). */
+static void canon_face(const double* P, int nv, double S[3], double X[3]) {
+  double e1[3], e2[3];
+  for (int d = 0; d < 3; ++d) {
+    e1[d] = nv == 3 ? P[3 + d] - P[d] : P[6 + d] - P[d];
+    e2[d] = nv == 3 ? P[6 + d] - P[d] : P[9 + d] - P[3 + d];
+  }
+  S[0] = 0.5 * (e1[1] * e2[2] - e1[2] * e2[1]);
+  S[1] = 0.5 * (e1[2] * e2[0] - e1[0] * e2[2]);
+  S[2] = 0.5 * (e1[0] * e2[1] - e1[1] * e2[0]);
+  for (int d = 0; d < 3; ++d) {
+    double a = P[d];
+    for (int i = 1; i < nv; ++i) a = a + P[3 * i + d];
+    X[d] = a / (double)nv;
+  }
+}
+
 static double det3(const double a[3], const double b[3], const double c[3]) {
   double x[3];
   cross(b, c, x);
@@ -457,6 +480,40 @@ int orc_mesh_build(orc_mesh* M, int64_t n_nodes, const double* xyz, int64_t n_ce
   for (int64_t c = 0; c < n_cells; ++c)
     for (int lf = 0; lf < ctype[c]; ++lf)
       if (M->cf[6 * c + lf] < 0) FAIL("cell %lld local face %d unassigned", (long long)c, lf);
+  /* geometry of the coarsening */
+  M->cvol = malloc(sizeof(double) * n_cells);
+  M->cctr = malloc(sizeof(double) * 3 * n_cells);
+  M->cSn = malloc(sizeof(double) * 3 * (nf ? nf : 1));
+  M->carea = malloc(sizeof(double) * (nf ? nf : 1));
+  M->camom = malloc(sizeof(double) * 3 * (nf ? nf : 1));
+  for (int64_t c = 0; c < n_cells; ++c) {
+    int nn = (int)(cell_ptr[c + 1] - cell_ptr[c]);
+    for (int d = 0; d < 3; ++d) {
+      double a = xyz[3 * (int64_t)cell_nodes[cell_ptr[c]] + d];
+      for (int i = 1; i < nn; ++i) a = a + xyz[3 * (int64_t)cell_nodes[cell_ptr[c] + i] + d];
+      M->cctr[3 * c + d] = a / (double)nn;
+    }
+    double v = 0.0;
+    for (int lf = 0; lf < ctype[c]; ++lf) {
+      int32_t nodes[4];
+      int nv = local_face(ctype[c], lf, cell_nodes + cell_ptr[c], nodes);
+      double P[12], S[3], X[3];
+      for (int i = 0; i < nv; ++i)
+        for (int d = 0; d < 3; ++d) P[3 * i + d] = xyz[3 * (int64_t)nodes[i] + d];
+      canon_face(P, nv, S, X);
+      v = v + (X[0] * S[0] + X[1] * S[1] + X[2] * S[2]);
+      if (M->cside[6 * c + lf] == 0) { /* the face seen from its left cell */
+        int32_t f = M->cf[6 * c + lf];
+        double a = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+        M->carea[f] = a;
+        for (int d = 0; d < 3; ++d) {
+          M->cSn[3 * f + d] = S[d];
+          M->camom[3 * f + d] = a * X[d];
+        }
+      }
+    }
+    M->cvol[c] = v / 3.0;
+  }
 done:
   free(recs);
   free(brecs);
@@ -495,6 +552,11 @@ void orc_mesh_free(orc_mesh* M) {
   free(M->ftag);
   free(M->ftagR);
   free(M->fngp);
+  free(M->cvol);
+  free(M->cctr);
+  free(M->cSn);
+  free(M->carea);
+  free(M->camom);
   free(M->shift);
   free(M->gx);
   free(M->gA);

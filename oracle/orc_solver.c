@@ -529,6 +529,38 @@ static int coarse_update(orc_solver* S, const orc_level* L, double* Wk, const do
   return 0;
 }
 
+/* W_i += r c_i on the receiving level L: c_i the injected correction Wc - Wc0 of the coarse cell of
+   i (prolongation 0), or the volume-weighted mean of the injected corrections of i and its face
+   neighbours, in ascending face order (prolongation 1); skipped where rho or p would not stay
+   positive (counted) */
+static void prolong_correction(orc_solver* S, const orc_level* L, const int32_t* f2c, const double* Wc,
+                               const double* Wc0, double* Wf) {
+  const double r = S->P.correction_relax;
+  for (int64_t i = 0; i < L->nc; ++i) {
+    double c[5], w[5];
+    int32_t k = f2c[i];
+    for (int q = 0; q < 5; ++q) c[q] = Wc[5 * k + q] - Wc0[5 * k + q];
+    if (S->P.prolongation == 1) {
+      double sv = L->vol[i];
+      for (int q = 0; q < 5; ++q) c[q] *= L->vol[i];
+      for (int32_t e = L->c2f_ptr[i]; e < L->c2f_ptr[i + 1]; ++e) {
+        int32_t f = L->c2f[e], a = L->fL[f], b = L->fR[f];
+        if (b < 0 || a == b) continue;
+        int64_t j = a == i ? b : a;
+        int32_t kj = f2c[j];
+        for (int q = 0; q < 5; ++q) c[q] += L->vol[j] * (Wc[5 * kj + q] - Wc0[5 * kj + q]);
+        sv += L->vol[j];
+      }
+      for (int q = 0; q < 5; ++q) c[q] /= sv;
+    }
+    for (int q = 0; q < 5; ++q) w[q] = Wf[5 * i + q] + r * c[q];
+    if (physical(w, S->P.gamma))
+      memcpy(Wf + 5 * i, w, sizeof(w));
+    else
+      S->skipped_corrections++;
+  }
+}
+
 /* one coarse smoothing step on level l: forward Euler, or LU-SGS on the defect R + F (Sec. 4.3) */
 static int coarse_smooth(orc_solver* S, int l, double* Wk, const double* R, const double* F, const double* dt) {
   const orc_level* L = &S->M->lev[l];
@@ -612,16 +644,7 @@ static int coarse_cycle(orc_solver* S, int l, double* Wk, const double* Rstar) {
       for (int q = 0; q < 5; ++q) Wc[5 * c + q] /= C->vol[c];
     memcpy(Wc0, Wc, sizeof(double) * 5 * m);
     rc = coarse_cycle(S, l + 1, Wc, Rc);
-    if (!rc)
-      for (int64_t i = 0; i < n; ++i) {
-        int32_t c = C->fine2coarse[i];
-        double w[5];
-        for (int q = 0; q < 5; ++q) w[q] = Wk[5 * i + q] + S->P.correction_relax * (Wc[5 * c + q] - Wc0[5 * c + q]);
-        if (physical(w, S->P.gamma))
-          memcpy(Wk + 5 * i, w, sizeof(w));
-        else
-          S->skipped_corrections++;
-      }
+    if (!rc) prolong_correction(S, L, C->fine2coarse, Wc, Wc0, Wk);
     free(Wc);
     free(Rc);
     free(Wc0);
@@ -662,7 +685,7 @@ static int vcycle(orc_solver* S, double* norm) {
   for (int64_t i = 0; i < nc; ++i) {
     int32_t c = C->fine2coarse[i];
     for (int q = 0; q < 5; ++q) {
-      Wc[5 * c + q] += M->vol[i] * S->W[5 * i + q];
+      Wc[5 * c + q] += M->cvol[i] * S->W[5 * i + q];
       Rc[5 * c + q] += res[5 * i + q];
     }
   }
@@ -670,15 +693,7 @@ static int vcycle(orc_solver* S, double* norm) {
     for (int q = 0; q < 5; ++q) Wc[5 * c + q] /= C->vol[c];
   memcpy(Wc0, Wc, sizeof(double) * 5 * m);
   if ((rc = coarse_cycle(S, 1, Wc, Rc))) goto out;
-  for (int64_t i = 0; i < nc; ++i) {
-    int32_t c = C->fine2coarse[i];
-    double w[5];
-    for (int q = 0; q < 5; ++q) w[q] = S->W[5 * i + q] + S->P.correction_relax * (Wc[5 * c + q] - Wc0[5 * c + q]);
-    if (physical(w, S->P.gamma))
-      memcpy(S->W + 5 * i, w, sizeof(w));
-    else
-      S->skipped_corrections++;
-  }
+  prolong_correction(S, &M->lev[0], C->fine2coarse, Wc, Wc0, S->W);
   for (int s = 0; s < S->P.post; ++s)
     if ((rc = fine_step(S, NULL))) goto out;
 out:

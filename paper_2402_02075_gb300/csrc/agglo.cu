@@ -250,13 +250,13 @@ __global__ void k_coarse_face_write(Level P, const int32_t* partner, const int32
       }
     }
     const double sg = q.flip ? -1.0 : 1.0;
-    Q.area[f] += P.area[g];
+    Q.area[f] = __dadd_rn(Q.area[f], P.area[g]);
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
-      Q.Sn[e * nfQ + f] += sg * P.Sn[e * nfP + g];
+      Q.Sn[e * nfQ + f] = __dadd_rn(Q.Sn[e * nfQ + f], sg * P.Sn[e * nfP + g]);
       double mom = P.amom[e * nfP + g];
-      if (q.flip) mom = mom - P.area[g] * P.shift[e * nfP + g];
-      Q.amom[e * nfQ + f] += mom;
+      if (q.flip) mom = __dsub_rn(mom, __dmul_rn(P.area[g], P.shift[e * nfP + g]));
+      Q.amom[e * nfQ + f] = __dadd_rn(Q.amom[e * nfQ + f], mom);
     }
   }
 }
@@ -427,7 +427,8 @@ cgks_status build_levels(cgks_ctx* ctx) {
   if (nl > 8) return cgks_fail(ctx, CGKS_EINVAL, "at most 8 multigrid levels");
   ctx->L.resize(1);
   for (int l = 1; l < nl; ++l) {
-    const Level& prev = ctx->L[l - 1];
+    // level 1 is built from the coarsening's own geometry of level 0 (identical in any implementation)
+    const Level& prev = l == 1 ? ctx->L0c : ctx->L[l - 1];
     int32_t* comp;
     CKS(dalloc(ctx, M, &comp, prev.nc));
     k_iota<<<grid_for(prev.nc, 256), 256, 0, st>>>(prev.nc, comp);

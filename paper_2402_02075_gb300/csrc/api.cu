@@ -256,6 +256,7 @@ static cgks_status check_params(cgks_ctx* ctx, const cgks_params* p) {
     return cgks_fail(ctx, CGKS_EINVAL, "correction_relax must be in (0, 1]");
   if (p->coarse_smoother != 0 && p->coarse_smoother != 1)
     return cgks_fail(ctx, CGKS_EINVAL, "coarse_smoother must be 0 or 1");
+  if (p->prolongation != 0 && p->prolongation != 1) return cgks_fail(ctx, CGKS_EINVAL, "prolongation must be 0 or 1");
   return CGKS_OK;
 }
 

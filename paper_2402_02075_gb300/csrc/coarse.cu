@@ -191,6 +191,58 @@ __global__ void k_prolong(int64_t ncf, int64_t ncc, const int32_t* __restrict__ 
   }
 }
 
+// prolongation 1: cell i of the receiving level takes the volume-weighted mean of the injected
+// corrections of itself and its face neighbours (in ascending face order), then W += relax x that
+__global__ void k_prolong_smooth(int64_t ncf, int64_t ncc, const int32_t* __restrict__ ptr,
+                                 const int32_t* __restrict__ c2f, const int32_t* __restrict__ fL,
+                                 const int32_t* __restrict__ fR, const double* __restrict__ vol,
+                                 const int32_t* __restrict__ f2c, const double* __restrict__ Wc,
+                                 const double* __restrict__ Wc0, double* __restrict__ Wf, double gamma, double relax,
+                                 unsigned long long* skipped) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= ncf) return;
+  double acc[5], sv = vol[i];
+  {
+    const int64_t c = f2c[i];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) acc[q] = vol[i] * (Wc[q * ncc + c] - Wc0[q * ncc + c]);
+  }
+  for (int32_t k = ptr[i]; k < ptr[i + 1]; ++k) {
+    const int64_t f = c2f[k];
+    const int32_t a = fL[f], b = fR[f];
+    if (b < 0 || a == b) continue;
+    const int64_t j = a == i ? b : a;
+    const int64_t c = f2c[j];
+    const double v = vol[j];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) acc[q] += v * (Wc[q * ncc + c] - Wc0[q * ncc + c]);
+    sv += v;
+  }
+  double w[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) w[q] = Wf[q * ncf + i] + relax * (acc[q] / sv);
+  const double p = (gamma - 1.0) * (w[4] - 0.5 * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]) / w[0]);
+  if (w[0] > 0.0 && p > 0.0) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) Wf[q * ncf + i] = w[q];
+  } else {
+    atomicAdd(skipped, 1ULL);
+  }
+}
+
+static void prolong(cgks_ctx* ctx, int lev_fine, const int32_t* f2c, int64_t ncc, const double* Wc,
+                    const double* Wc0, double* Wf) {
+  const Level& L = ctx->L[lev_fine];
+  cudaStream_t st = ctx->stream;
+  if (ctx->P.prolongation == 1)
+    k_prolong_smooth<<<grid_for(L.nc, 256), 256, 0, st>>>(L.nc, ncc, L.c2f_ptr, L.c2f, L.fL, L.fR, L.vol, f2c, Wc, Wc0,
+                                                           Wf, ctx->P.gamma, ctx->P.correction_relax,
+                                                           (unsigned long long*)ctx->d_skipped);
+  else
+    k_prolong<<<grid_for(L.nc, 256), 256, 0, st>>>(L.nc, ncc, f2c, Wc, Wc0, Wf, ctx->P.gamma, ctx->P.correction_relax,
+                                                   (unsigned long long*)ctx->d_skipped);
+}
+
 // sqrt(mean (res_rho / V)^2): per-block partial sums, then one thread adds them in block order
 __global__ void k_norm_partial(int64_t n, const double* __restrict__ res, const double* __restrict__ vol,
                                double* __restrict__ part) {
@@ -307,8 +359,7 @@ static cgks_status coarse_cycle(cgks_ctx* ctx, int l) {
                                                      N.W, N.Rs);
     CK(cudaMemcpyAsync(N.W0, N.W, sizeof(double) * 5 * Cn.nc, cudaMemcpyDeviceToDevice, st));
     CKS(coarse_cycle(ctx, l + 1));
-    k_prolong<<<grid_for(L.nc, 256), 256, 0, st>>>(L.nc, Cn.nc, Cn.f2c, N.W, N.W0, B.W, ctx->P.gamma, ctx->P.correction_relax,
-                                                   (unsigned long long*)ctx->d_skipped);
+    prolong(ctx, l, Cn.f2c, Cn.nc, N.W, N.W0, B.W);
     for (int s = 0; s < ctx->P.post; ++s) {
       CKS(coarse_residual(ctx, l));
       CKS(coarse_smooth(ctx, l));
@@ -339,12 +390,11 @@ cgks_status vcycle_once(cgks_ctx* ctx, double* norm_dev) {
   // defect at the smoothed state (gradient and compression outputs discarded)
   CKS(fine_fluxes(ctx, ctx->W, ctx->G, ctx->alpha));
   CKS(fine_gather(ctx, ctx->W, nullptr, ctx->res, nullptr, nullptr, 0));
-  k_restrict<<<grid_for(C1.nc, 256), 256, 0, st>>>(C1.nc, F.nc, C1.agg_ptr, C1.agg, F.vol, C1.vol, ctx->W, ctx->res,
+  k_restrict<<<grid_for(C1.nc, 256), 256, 0, st>>>(C1.nc, F.nc, C1.agg_ptr, C1.agg, ctx->L0c.vol, C1.vol, ctx->W, ctx->res,
                                                    nullptr, B1.W, B1.Rs);
   CK(cudaMemcpyAsync(B1.W0, B1.W, sizeof(double) * 5 * C1.nc, cudaMemcpyDeviceToDevice, st));
   CKS(coarse_cycle(ctx, 1));
-  k_prolong<<<grid_for(F.nc, 256), 256, 0, st>>>(F.nc, C1.nc, C1.f2c, B1.W, B1.W0, ctx->W, ctx->P.gamma, ctx->P.correction_relax,
-                                                 (unsigned long long*)ctx->d_skipped);
+  prolong(ctx, 0, C1.f2c, C1.nc, B1.W, B1.W0, ctx->W);
   for (int s = 0; s < ctx->P.post; ++s) CKS(step_once(ctx, nullptr));
   CK(cudaGetLastError());
   return CGKS_OK;

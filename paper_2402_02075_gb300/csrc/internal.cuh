@@ -89,6 +89,7 @@ struct cgks_ctx {
   bool has_mesh = false, has_state = false;
   Fine F;
   std::vector<Level> L;  // L[0] is the fine level seen as a first-order mesh
+  Level L0c;             // L[0] with the geometry of the coarsening (input of level 1, restriction weights)
   std::vector<CoarseBuf> C;
   // fine state and work arrays
   double *W = nullptr, *G = nullptr, *alpha = nullptr;

@@ -21,6 +21,77 @@ __constant__ int8_t c_lface[3][6][4] = {
 
 __device__ __forceinline__ int lface_nv(int t, int lf) { return c_lface[t - 4][lf][3] < 0 ? 3 : 4; }
 
+// ---- geometry of the coarsening ------------------------------------------------------------------
+// The agglomeration decides merges by comparing a skewness measure with a limit, so its geometric
+// inputs are defined by one formula evaluated with a fixed sequence of correctly rounded operations
+// (no contraction into FMA): the same values on every machine and in any independent implementation
+// of the formula.  A face of nodes P_0..P_{n-1} (the left cell's local order): area vector
+// 1/2 (P_1 - P_0) x (P_2 - P_0) for a triangle, 1/2 (P_2 - P_0) x (P_3 - P_1) for a quadrilateral
+// (both exact for flat triangles and bilinear quadrilaterals), centre the node mean, area the length
+// of the area vector.  A cell: centre the node mean, volume 1/3 sum over its faces (own local order,
+// outward) of centre . area vector.
+__device__ __forceinline__ void canon_face(const double P[4][3], int nv, double S[3], double X[3]) {
+  double e1[3], e2[3];
+  for (int d = 0; d < 3; ++d) {
+    e1[d] = nv == 3 ? __dsub_rn(P[1][d], P[0][d]) : __dsub_rn(P[2][d], P[0][d]);
+    e2[d] = nv == 3 ? __dsub_rn(P[2][d], P[0][d]) : __dsub_rn(P[3][d], P[1][d]);
+  }
+  S[0] = __dmul_rn(0.5, __dsub_rn(__dmul_rn(e1[1], e2[2]), __dmul_rn(e1[2], e2[1])));
+  S[1] = __dmul_rn(0.5, __dsub_rn(__dmul_rn(e1[2], e2[0]), __dmul_rn(e1[0], e2[2])));
+  S[2] = __dmul_rn(0.5, __dsub_rn(__dmul_rn(e1[0], e2[1]), __dmul_rn(e1[1], e2[0])));
+  for (int d = 0; d < 3; ++d) {
+    double a = P[0][d];
+    for (int i = 1; i < nv; ++i) a = __dadd_rn(a, P[i][d]);
+    X[d] = __ddiv_rn(a, (double)nv);
+  }
+}
+
+__global__ void k_canon_faces(int64_t nf, const int32_t* fL, const int32_t* flf, const int8_t* ctype,
+                              const int64_t* cptr, const int32_t* cn, const double* xyz, double* Sn, double* area,
+                              double* amom) {
+  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= nf) return;
+  const int64_t c = fL[f];
+  const int t = ctype[c], lf = flf[f], nv = lface_nv(t, lf);
+  double P[4][3], S[3], X[3];
+  for (int i = 0; i < nv; ++i) {
+    const int64_t node = cn[cptr[c] + c_lface[t - 4][lf][i]];
+    for (int d = 0; d < 3; ++d) P[i][d] = xyz[3 * node + d];
+  }
+  canon_face(P, nv, S, X);
+  const double a = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(S[0], S[0]), __dmul_rn(S[1], S[1])), __dmul_rn(S[2], S[2])));
+  area[f] = a;
+  for (int d = 0; d < 3; ++d) {
+    Sn[d * nf + f] = S[d];
+    amom[d * nf + f] = __dmul_rn(a, X[d]);
+  }
+}
+
+__global__ void k_canon_cells(int64_t nc, const int8_t* ctype, const int64_t* cptr, const int32_t* cn,
+                              const double* xyz, double* vol, double* ctr) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  const int t = ctype[c];
+  const int nn = t == 4 ? 4 : (t == 5 ? 6 : 8);
+  for (int d = 0; d < 3; ++d) {
+    double a = xyz[3 * (int64_t)cn[cptr[c]] + d];
+    for (int i = 1; i < nn; ++i) a = __dadd_rn(a, xyz[3 * (int64_t)cn[cptr[c] + i] + d]);
+    ctr[d * nc + c] = __ddiv_rn(a, (double)nn);
+  }
+  double v = 0.0;
+  for (int lf = 0; lf < t; ++lf) {
+    const int nv = lface_nv(t, lf);
+    double P[4][3], S[3], X[3];
+    for (int i = 0; i < nv; ++i) {
+      const int64_t node = cn[cptr[c] + c_lface[t - 4][lf][i]];
+      for (int d = 0; d < 3; ++d) P[i][d] = xyz[3 * node + d];
+    }
+    canon_face(P, nv, S, X);
+    v = __dadd_rn(v, __dadd_rn(__dadd_rn(__dmul_rn(X[0], S[0]), __dmul_rn(X[1], S[1])), __dmul_rn(X[2], S[2])));
+  }
+  vol[c] = __ddiv_rn(v, 3.0);
+}
+
 struct Key4 {
   int32_t v[4];
 };
@@ -857,6 +928,17 @@ cgks_status build_fine_mesh(cgks_ctx* ctx, int64_t n_nodes, const double* xyz, i
   L0.c2f = F.c2f;
   ctx->L.clear();
   ctx->L.push_back(L0);
+  // level 0 as seen by the coarsening: same topology, geometry of the coarsening
+  Level Lc = L0;
+  CKS(dalloc(ctx, M, &Lc.vol, nc));
+  CKS(dalloc(ctx, M, &Lc.ctr, 3 * nc));
+  CKS(dalloc(ctx, M, &Lc.Sn, 3 * nf));
+  CKS(dalloc(ctx, M, &Lc.area, nf));
+  CKS(dalloc(ctx, M, &Lc.amom, 3 * nf));
+  k_canon_faces<<<grid_for(nf, B), B, 0, st>>>(nf, F.fL, F.flf, d_ct, d_cptr, d_cn, d_xyz, Lc.Sn, Lc.area, Lc.amom);
+  k_canon_cells<<<grid_for(nc, 128), 128, 0, st>>>(nc, d_ct, d_cptr, d_cn, d_xyz, Lc.vol, Lc.ctr);
+  CK(cudaGetLastError());
+  ctx->L0c = Lc;
   CK(cudaStreamSynchronize(st));
   return CGKS_OK;
 }

@@ -220,12 +220,14 @@ def test_vcycles_with_lusgs_coarse_smoother(cg, orc, case):
     assert ctx.skipped_updates() == os_.skipped()
 
 
-def test_vcycles_with_relaxed_correction(cg, orc):
-    """correction_relax r < 1 scales the injected coarse correction on every level, the same way in
-    the oracle."""
+@pytest.mark.parametrize("extra", [dict(correction_relax=0.5), dict(prolongation=1),
+                                   dict(prolongation=1, correction_relax=0.7)])
+def test_vcycles_with_relaxed_or_smoothed_correction(cg, orc, extra):
+    """correction_relax r < 1 scales the injected coarse correction and prolongation 1 averages it
+    over face neighbours, on every level, the same way in the oracle."""
     mesh = mg.wall_box(16, 8, 16, n_prism=6)
     W, G = mg.uniform_state(len(mesh["cell_type"]), mach=0.5)
-    prm = dict(mach=0.5, viscous=1, reynolds=1e4, prandtl=0.72, correction_relax=0.5)
+    prm = dict(mach=0.5, viscous=1, reynolds=1e4, prandtl=0.72, **extra)
     ctx, om, os_ = _pair(cg, orc, mesh, W, G, n_levels=3, **prm)
     hg = ctx.vcycle(3)
     ho = os_.run(3, multigrid=True)

@@ -33,7 +33,9 @@ def _levels(orc, mesh, **kw):
 def test_partition_and_volume_invariants(orc, mk):
     mesh = mk()
     M, S = _levels(orc, mesh, n_levels=3)
-    prev = S.level(0)
+    prev = dict(S.level(0))
+    # level 1 aggregates the coarsening's own geometry of the fine level
+    prev["vol"], prev["ctr"], _, _ = M.coarsening_geometry()
     for lev in (1, 2):
         L = S.level(lev)
         m = L["map"]

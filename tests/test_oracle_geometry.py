@@ -185,3 +185,35 @@ def test_weno_falls_back_towards_p1_at_a_discontinuity(orc):
     near = np.abs(ctr[:, 0] - 0.5) < 0.1
     assert np.all(np.abs(p2[near]) > 10.0)
     assert np.all(np.abs(r[near]) < 0.3 * np.abs(p2[near]))
+
+
+def test_coarsening_geometry(orc):
+    """The coarsening's geometry: node-mean centres, face area vectors from the diagonals (exact for
+    flat triangles and bilinear quadrilaterals), divergence-theorem volumes.  On an unjittered mixed
+    box every face is flat, so volumes and area vectors equal the quadrature ones and the cells
+    close; tetrahedron centres are centroids."""
+    mesh = mg.periodic_box(6, jitter=0.0) if "jitter" in mg.periodic_box.__code__.co_varnames else None
+    if mesh is None:
+        pytest.skip("periodic_box without a jitter argument")
+    M = orc.Mesh(mesh)
+    vol, ctr, Sn, area = M.coarsening_geometry()
+    rvol, rctr, _ = M.cells()
+    np.testing.assert_allclose(vol, rvol, rtol=1e-13)
+    np.testing.assert_allclose(area, np.linalg.norm(Sn, axis=1), rtol=1e-15)
+    F = M.faces()
+    qS = F["gA"].sum(axis=1)
+    np.testing.assert_allclose(Sn, qS, rtol=0, atol=1e-15 * np.abs(qS).max())
+    tets = np.asarray(mesh["cell_type"]) == 4
+    np.testing.assert_allclose(ctr[tets], rctr[tets], rtol=0, atol=1e-15)
+    nodes = mesh["xyz"][mesh["cell_nodes"]]
+    owner = np.repeat(np.arange(len(mesh["cell_type"])), np.diff(mesh["cell_ptr"]))
+    mean = np.zeros((len(mesh["cell_type"]), 3))
+    np.add.at(mean, owner, nodes)
+    mean /= np.diff(mesh["cell_ptr"])[:, None]
+    np.testing.assert_allclose(ctr, mean, rtol=0, atol=1e-15)
+    # closure of every cell: the outward canonical area vectors of its faces sum to zero
+    clos = np.zeros((M.nc, 3))
+    np.add.at(clos, F["fL"], Sn)
+    inner = F["fR"] >= 0
+    np.add.at(clos, F["fR"][inner], -Sn[inner])
+    assert np.abs(clos).max() < 1e-15
