@@ -136,6 +136,23 @@ def dist_env():
     return rank, world, local
 
 
+def reduce_max(x, world, device):
+    """Largest x over the ranks of the process group (x itself on one rank)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(cells_per_replica, steps, ms_max, world):
+    """Whole-job Mcell-iters/s: every replica advanced its cells `steps` times, and the job took
+    the slowest rank's time."""
+    return world * cells_per_replica * steps / (ms_max * 1e-3) / 1e6
+
+
 def cpu_baseline(steps_per_sample=6):
     """The oracle (as it stands) on a bounded sample of the workload: V-cycles per second x cells."""
     import meshgen as mg
@@ -182,7 +199,8 @@ def converge_cases(slab):
 
 def run_converge(cg, torch, slab):
     """Wall time (host clock around the library's own steady-solve loop) to a 1e-10 drop of the
-    density residual for single-grid FP64 CGKS, the FP64 V-cycle and the mixed V-cycle."""
+    density residual for single-grid FP64 CGKS, the FP64 V-cycle, the mixed V-cycle and the FP64
+    V-cycle with the LU-SGS coarse smoother (Sec. 4.3)."""
     import numpy as np
     import meshgen as mg
     out = []
@@ -190,8 +208,9 @@ def run_converge(cg, torch, slab):
         mesh = mk()
         row = {"case": name, "cells": len(mesh["cell_type"])}
         states = {}
-        for key, mgrid, prec in (("single_grid_fp64", False, 0), ("vcycle_fp64", True, 0), ("vcycle_mixed", True, 1)):
-            P = cg.default_params(n_levels=3, precision=prec, **phys)
+        for key, mgrid, prec, sm in (("single_grid_fp64", False, 0, 0), ("vcycle_fp64", True, 0, 0),
+                                     ("vcycle_mixed", True, 1, 0), ("vcycle_fp64_lusgs", True, 0, 1)):
+            P = cg.default_params(n_levels=3, precision=prec, coarse_smoother=sm, **phys)
             ctx = cg.upload_mesh(mesh, P)
             W, G = mg.uniform_state(ctx.nc, mach=phys["mach"])
             ctx.state_init(torch.from_numpy(W).cuda(), torch.from_numpy(G).cuda())
@@ -272,11 +291,7 @@ def main():
             dist.barrier()
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(x, world, "cuda")
 
     mesh = mg.wall_box(**WORKLOAD)
     P = cg.default_params(**PARAMS)
@@ -313,7 +328,7 @@ def main():
     g_ms, g_n = ctx.kernel_stats(2)
     ctx.profile(False)
     ms_max = max_over_ranks(ms)
-    value = world * nc * args.steps / (ms_max * 1e-3) / 1e6
+    value = job_rate(nc, args.steps, ms_max, world)
     # end to end through the public API with host buffers: per step, the state is copied in from
     # pinned host memory (cgks_state_init) and the residual norm is read back (cgks_vcycle)
     Wo, Go, ao = ctx.state_get()
@@ -326,7 +341,7 @@ def main():
         ctx.vcycle(1, history=True)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0)
-    e2e = {"value": world * nc * args.steps / e2e_s / 1e6, "unit": UNIT,
+    e2e = {"value": job_rate(nc, args.steps, e2e_s * 1e3, world), "unit": UNIT,
            "h2d_bytes_per_step": int(Wh.numel() + Gh.numel() + ah.numel()) * 8, "d2h_bytes_per_step": 8}
     # the mixed-precision V-cycle on the same workload: coarse levels in FP32 defect-correction form
     ctx.set_params(cg.default_params(precision=1, **PARAMS))
@@ -341,7 +356,7 @@ def main():
     barrier()
     ms_mixed = max_over_ranks(ev0.elapsed_time(ev1))
     Pm = ctx.params
-    mixed = {"value": world * nc * args.steps / (ms_mixed * 1e-3) / 1e6, "unit": UNIT,
+    mixed = {"value": job_rate(nc, args.steps, ms_mixed, world), "unit": UNIT,
              "ms_per_step": ms_mixed / args.steps,
              "gpu_launches": launches_per_vcycle({f: getattr(Pm, f) for f in (
                  "dt_mode", "pre", "post", "n_levels", "coarse_steps", "precision")}) * args.steps,
