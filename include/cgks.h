@@ -52,6 +52,9 @@ typedef struct {
   double c_press;      /* C of the pressure-jump term of tau_n (Sec. 2.3, 1) */
   double weno_eps;     /* epsilon of the non-linear WENO weights (Sec. 3.4, 1e-5) */
   double skew_min;     /* skewness limit of the coarsening (Sec. 4.1; no value given, 0.2) */
+  double sutherland;   /* Sutherland constant over the free-stream temperature, S/T_inf (0.383 for air
+                          at 288 K): mu = mu_inf t^(3/2) (1 + s)/(t + s), t = T/T_inf; 0 (the default)
+                          keeps mu constant */
   double correction_relax; /* factor on the injected coarse correction W += r (W_c - W_c^0); Sec. 4.2
                               injects the plain correction (1, the default) */
   int32_t n_levels;    /* multigrid levels including the fine one (Sec. 4.2 uses 3) */

@@ -17,7 +17,7 @@
 
 typedef struct {
   double gamma, mach, reynolds, prandtl, aoa[2], cfl_fine, cfl_coarse, eps_inviscid, c_press,
-      weno_eps, skew_min, correction_relax;
+      weno_eps, skew_min, sutherland, correction_relax;
   int32_t n_levels, pre, post, coarse_steps, passes_per_level, viscous, dt_mode, precision;
   int32_t coarse_smoother; /* 0 forward Euler, 1 LU-SGS (Sec. 4.3) */
   int32_t prolongation;    /* 0 injection, 1 injection smoothed over face neighbours */
@@ -76,10 +76,13 @@ int orc_prim_from_cons(const double W[5], double gamma, orc_maxw* g);
 void orc_frame(const double n[3], double t1[3], double t2[3]);
 void orc_time_integrals(double dt, double tau, double tau_n, double q[5]);
 typedef struct {
-  double gamma, K, mu, prandtl, eps_inviscid, c_press;
+  double gamma, K, mu, prandtl, eps_inviscid, c_press, sutherland;
   int viscous;
   double Winf[5];
 } orc_phys;
+/* dynamic viscosity at t = T/T_inf = gamma p / rho: constant mu_inf, or Sutherland's law
+   mu_inf t^(3/2) (1 + s)/(t + s) with s = S/T_inf */
+double orc_viscosity(const orc_phys* ph, double t);
 int orc_gks_point(const orc_phys* ph, const double WL[5], const double GL[15], const double WR[5],
                   const double GR[15], const double n[3], double dt, double F[5], double Wt[5]);
 int orc_kfvs_point(const orc_phys* ph, const double WL[5], const double WR[5], const double n[3], double F[5]);

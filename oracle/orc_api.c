@@ -266,6 +266,7 @@ static void phys_of(const orc_params* P, orc_phys* ph) {
   ph->c_press = P->c_press;
   ph->viscous = P->viscous;
   ph->mu = P->viscous ? P->mach / P->reynolds : 0.0;
+  ph->sutherland = P->sutherland;
   double a = P->aoa[0] * M_PI / 180.0, b = P->aoa[1] * M_PI / 180.0;
   double u[3] = {P->mach * cos(a) * cos(b), P->mach * sin(b), P->mach * sin(a) * cos(b)};
   ph->Winf[0] = 1.0;

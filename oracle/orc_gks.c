@@ -127,6 +127,11 @@ void orc_frame(const double n[3], double t1[3], double t2[3]) {
 }
 
 /* exact integrals over [0, dt] of the time coefficients of Eq. 2nd-flux */
+double orc_viscosity(const orc_phys* ph, double t) {
+  if (ph->sutherland == 0.0) return ph->mu;
+  return ph->mu * pow(t, 1.5) * (1.0 + ph->sutherland) / (t + ph->sutherland);
+}
+
 void orc_time_integrals(double dt, double tau, double tn, double q[5]) {
   double e = exp(-dt / tn);
   q[0] = dt - tn * (1.0 - e);                                    /* 1 - e^{-t/tn}           */
@@ -217,7 +222,7 @@ int orc_gks_point(const orc_phys* ph, const double WL[5], const double GL[15], c
   double jump = fabs((pl - pr) / (pl + pr));
   double tau, tn;
   if (ph->viscous) {
-    tau = ph->mu / pc;
+    tau = orc_viscosity(ph, ph->gamma * pc / wc[0]) / pc; /* mu(T^c) / p^c */
     tn = tau + ph->c_press * jump * dt;
   } else {
     tn = ph->eps_inviscid * dt + ph->c_press * jump * dt;

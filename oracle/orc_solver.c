@@ -307,7 +307,7 @@ static void local_dt_fine(const orc_solver* S, const double* W, double* dt) {
     const double* w = W + 5 * i;
     double rho = w[0], u[3] = {w[1] / rho, w[2] / rho, w[3] / rho};
     double p = (g - 1.0) * (w[4] - 0.5 * rho * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
-    double c = sqrt(g * p / rho), nu = S->P.viscous ? S->ph.mu / rho : 0.0;
+    double c = sqrt(g * p / rho), nu = S->P.viscous ? orc_viscosity(&S->ph, g * p / rho) / rho : 0.0;
     double sum = 0.0, V = M->vol[i];
     for (int m = 0; m < M->ctype[i]; ++m) {
       int64_t f = M->cf[6 * i + m];
@@ -725,6 +725,7 @@ orc_solver* orc_solver_new(orc_mesh* M, const orc_params* P, char* err) {
   for (int d = 0; d < 3; ++d) S->ph.Winf[1 + d] = rho * u[d];
   S->ph.Winf[4] = p / (g - 1.0) + 0.5 * rho * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
   S->ph.mu = P->viscous ? rho * P->mach * 1.0 / P->reynolds : 0.0;
+  S->ph.sutherland = P->sutherland;
   S->W = calloc(5 * M->nc, sizeof(double));
   S->G = calloc(15 * M->nc, sizeof(double));
   S->alpha = malloc(sizeof(double) * M->nc);

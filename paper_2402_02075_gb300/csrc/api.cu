@@ -45,6 +45,7 @@ Phys make_phys(const cgks_params& P) {
   ph.prandtl = P.prandtl;
   ph.eps_inviscid = P.eps_inviscid;
   ph.c_press = P.c_press;
+  ph.suth = P.sutherland;
   ph.weno_eps = P.weno_eps;
   ph.cfl_fine = P.cfl_fine;
   ph.cfl_coarse = P.cfl_coarse;
@@ -249,6 +250,7 @@ static cgks_status check_params(cgks_ctx* ctx, const cgks_params* p) {
   if (!(p->mach >= 0.0) || !(p->cfl_fine > 0.0) || !(p->cfl_coarse > 0.0)) return cgks_fail(ctx, CGKS_EINVAL, "mach/cfl");
   if (p->viscous && !(p->reynolds > 0.0)) return cgks_fail(ctx, CGKS_EINVAL, "reynolds must be positive");
   if (!(p->prandtl > 0.0) || !(p->weno_eps > 0.0)) return cgks_fail(ctx, CGKS_EINVAL, "prandtl/weno_eps");
+  if (!(p->sutherland >= 0.0)) return cgks_fail(ctx, CGKS_EINVAL, "sutherland must be >= 0");
   if (p->n_levels < 1 || p->n_levels > 8 || p->passes_per_level < 0 || p->coarse_steps < 0 || p->pre < 0 || p->post < 0)
     return cgks_fail(ctx, CGKS_EINVAL, "multigrid counts out of range");
   if (p->precision != 0 && p->precision != 1) return cgks_fail(ctx, CGKS_EINVAL, "precision must be 0 or 1");

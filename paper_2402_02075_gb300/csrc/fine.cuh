@@ -26,6 +26,13 @@ HD double rsqrt_hd(double x) {
 #endif
 }
 
+// dynamic viscosity at temperature ratio t = T/T_inf = gamma p/rho (free stream rho 1, p 1/gamma):
+// constant, or Sutherland's law mu_inf t^(3/2) (1 + s)/(t + s)
+HD double viscosity(const Phys& ph, double t) {
+  if (ph.suth == 0.0) return ph.mu;
+  return ph.mu * t * sqrt(t) * (1.0 + ph.suth) / (t + ph.suth);
+}
+
 struct ReconArgs {
   int64_t nc, nf;
   const int8_t* ctype;
@@ -145,7 +152,7 @@ HD void reconstruct_body(int64_t i, const ReconArgs& a) {
   const double p = (ph.gamma - 1.0) * (Q0[4] - 0.5 * Q0[0] * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
   const double c = sqrt(ph.gamma * p * r);
   const double V = a.vol[i];
-  const double nu2 = ph.viscous ? 2.0 * ph.mu * r / V : 0.0;
+  const double nu2 = ph.viscous ? 2.0 * viscosity(ph, ph.gamma * p * r) * r / V : 0.0;
   double s = 0.0;
   for (int m = 0; m < nt; ++m) {
     const double S = a.dtw[(4 * m + 3) * nc + i];
@@ -471,7 +478,7 @@ HD void gks_point_body(int64_t g, const PointArgs& a) {
   const double jump = fabs((gl.p - gr.p) / (gl.p + gr.p));
   double tau, tn;
   if (ph.viscous) {
-    tau = ph.mu * (gc.r * gc.l2);  // mu / p^c
+    tau = viscosity(ph, ph.gamma * gc.h) * (gc.r * gc.l2);  // mu(T^c) / p^c, p^c/rho^c = 1/(2 lambda^c)
     tn = tau + ph.c_press * jump * dtf;
   } else {
     tn = (ph.eps_inviscid + ph.c_press * jump) * dtf;

@@ -237,3 +237,29 @@ def test_compression_factor_special_cases(orc):
     WL = np.array([1.0, 0.0, 0.0, 0.0, 2.0 / 0.4])
     WR = np.array([1.0, 0.0, 0.0, 0.0, 1.0 / 0.4])
     assert abs(orc.cf_alpha(prm, WL, WR, np.array([0.0, 1.0, 0])) - 1.0 / (1.0 + 2.25)) < 1e-15
+
+
+def _sutherland(t, s):
+    """Sutherland's law mu(T)/mu(T_inf) written out: t^(3/2) (1 + s) / (t + s)."""
+    return t ** 1.5 * (1.0 + s) / (t + s)
+
+
+def test_sutherland_viscosity_enters_as_mu_of_the_interface_temperature(orc):
+    """With Sutherland's law (s = 110.4 K / 288.15 K) the gas-kinetic flux of a smooth state at
+    temperature ratio t equals the constant-viscosity flux with mu = mu_inf x the law at t (the
+    interface equilibrium of a state without jumps has that temperature), and differs from the
+    constant-mu_inf flux; at t = 1 the law returns mu_inf."""
+    g, mach, re, s = 1.4, 0.5, 200.0, 110.4 / 288.15
+    rho, p = 0.9, 1.3 / 1.4
+    t = g * p / rho
+    u = np.array([0.4, 0.1, -0.05])
+    W = np.array([rho, *(rho * u), p / (g - 1) + 0.5 * rho * u @ u])
+    G = 0.05 * np.sin(np.arange(15) + 1.0)
+    n = np.array([0.6, 0.8, 0.0])
+    base = dict(gamma=g, mach=mach, viscous=1, prandtl=0.72)
+    Fs, Ws = orc.gks_point(orc.params(reynolds=re, sutherland=s, **base), W, G, W, G, n, 1e-3)
+    Fe, We = orc.gks_point(orc.params(reynolds=re / _sutherland(t, s), **base), W, G, W, G, n, 1e-3)
+    F0, _ = orc.gks_point(orc.params(reynolds=re, **base), W, G, W, G, n, 1e-3)
+    np.testing.assert_allclose(Fs, Fe, rtol=1e-12, atol=1e-15)
+    assert np.abs(Fs - F0).max() > 1e-6 * np.abs(F0).max()
+    assert _sutherland(1.0, s) == 1.0
