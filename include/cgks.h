@@ -69,6 +69,9 @@ typedef struct {
                           correction, cgks_kfvs_jvp); the fine level, the defect, its restriction,
                           the states, updates and correction stay FP64 */
   int32_t coarse_smoother; /* 0 forward Euler (Sec. 4.2); 1 LU-SGS, the implicit variant of Sec. 4.3 */
+  int32_t compression_factor; /* 1 (default): the gradient compression factor of Sec. 3.3; 0: alpha = 1
+                                 (no compression), for shock-free flows: its |p_l - p_r| terms are not
+                                 smooth at zero and hold V-cycles at a residual floor near convergence */
   int32_t prolongation;    /* 0 injection (Sec. 4.2); 1 injection smoothed once over face neighbours: a
                               cell receives the volume-weighted mean of its own and its neighbours'
                               injected corrections (not in the paper) */

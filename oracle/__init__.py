@@ -42,7 +42,7 @@ class Params(C.Structure):
                 ("weno_eps", C.c_double), ("skew_min", C.c_double), ("sutherland", C.c_double), ("correction_relax", C.c_double),
                 ("n_levels", C.c_int32), ("pre", C.c_int32), ("post", C.c_int32),
                 ("coarse_steps", C.c_int32), ("passes_per_level", C.c_int32), ("viscous", C.c_int32),
-                ("dt_mode", C.c_int32), ("precision", C.c_int32), ("coarse_smoother", C.c_int32), ("prolongation", C.c_int32),
+                ("dt_mode", C.c_int32), ("precision", C.c_int32), ("coarse_smoother", C.c_int32), ("compression_factor", C.c_int32), ("prolongation", C.c_int32),
                 ("agglo_seed", C.c_uint64)]
 
 
@@ -52,7 +52,7 @@ def params(**kw) -> Params:
     d = dict(gamma=1.4, mach=0.2, reynolds=1e4, prandtl=1.0, aoa=(0.0, 0.0), cfl_fine=0.5,
              cfl_coarse=0.5, eps_inviscid=0.01, c_press=1.0, weno_eps=1e-5, skew_min=0.2, sutherland=0.0, correction_relax=1.0,
              n_levels=3, pre=1, post=0, coarse_steps=1, passes_per_level=2, viscous=0,
-             dt_mode=0, precision=0, coarse_smoother=0, prolongation=0, agglo_seed=0)
+             dt_mode=0, precision=0, coarse_smoother=0, compression_factor=1, prolongation=0, agglo_seed=0)
     d.update(kw)
     p = Params()
     for k, v in d.items():

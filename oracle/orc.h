@@ -20,6 +20,7 @@ typedef struct {
       weno_eps, skew_min, sutherland, correction_relax;
   int32_t n_levels, pre, post, coarse_steps, passes_per_level, viscous, dt_mode, precision;
   int32_t coarse_smoother; /* 0 forward Euler, 1 LU-SGS (Sec. 4.3) */
+  int32_t compression_factor; /* 1 the CF of Sec. 3.3, 0 alpha = 1 */
   int32_t prolongation;    /* 0 injection, 1 injection smoothed over face neighbours */
   uint64_t agglo_seed;
 } orc_params;

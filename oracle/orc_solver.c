@@ -406,7 +406,7 @@ int orc_residual_fine(orc_solver* S, const double* W, const double* G, const dou
         for (int d = 0; d < 3; ++d) XR[d] = x[d] - M->shift[3 * f + d] - M->ctr[3 * R + d];
         eval_poly((const double(*)[10])(rc + 50 * R), XR, WR, GR);
         dtf = dt[L] < dt[R] ? dt[L] : dt[R];
-        ak = orc_cf_alpha(&S->ph, WL, WR, n);
+        ak = S->P.compression_factor ? orc_cf_alpha(&S->ph, WL, WR, n) : 1.0;
       } else {
         if (orc_bc_ghost(&S->ph, M->ftag[f], n, WL, GL, WR, GR)) bad |= 1;
         dtf = dt[L];

@@ -40,7 +40,7 @@ class Params(C.Structure):
                 ("eps_inviscid", C.c_double), ("c_press", C.c_double), ("weno_eps", C.c_double),
                 ("skew_min", C.c_double), ("sutherland", C.c_double), ("correction_relax", C.c_double), ("n_levels", C.c_int32), ("pre", C.c_int32), ("post", C.c_int32),
                 ("coarse_steps", C.c_int32), ("passes_per_level", C.c_int32), ("viscous", C.c_int32),
-                ("dt_mode", C.c_int32), ("precision", C.c_int32), ("coarse_smoother", C.c_int32), ("prolongation", C.c_int32),
+                ("dt_mode", C.c_int32), ("precision", C.c_int32), ("coarse_smoother", C.c_int32), ("compression_factor", C.c_int32), ("prolongation", C.c_int32),
                 ("agglo_seed", C.c_uint64)]
 
 

@@ -46,6 +46,7 @@ Phys make_phys(const cgks_params& P) {
   ph.eps_inviscid = P.eps_inviscid;
   ph.c_press = P.c_press;
   ph.suth = P.sutherland;
+  ph.cf = P.compression_factor;
   ph.weno_eps = P.weno_eps;
   ph.cfl_fine = P.cfl_fine;
   ph.cfl_coarse = P.cfl_coarse;
@@ -236,6 +237,7 @@ cgks_status cgks_default_params(cgks_params* p) {
   p->weno_eps = 1e-5;
   p->skew_min = 0.2;
   p->correction_relax = 1.0;
+  p->compression_factor = 1;
   p->n_levels = 3;
   p->pre = 1;
   p->post = 0;
@@ -258,6 +260,8 @@ static cgks_status check_params(cgks_ctx* ctx, const cgks_params* p) {
     return cgks_fail(ctx, CGKS_EINVAL, "correction_relax must be in (0, 1]");
   if (p->coarse_smoother != 0 && p->coarse_smoother != 1)
     return cgks_fail(ctx, CGKS_EINVAL, "coarse_smoother must be 0 or 1");
+  if (p->compression_factor != 0 && p->compression_factor != 1)
+    return cgks_fail(ctx, CGKS_EINVAL, "compression_factor must be 0 or 1");
   if (p->prolongation != 0 && p->prolongation != 1) return cgks_fail(ctx, CGKS_EINVAL, "prolongation must be 0 or 1");
   return CGKS_OK;
 }

@@ -493,7 +493,7 @@ HD void gks_point_body(int64_t g, const PointArgs& a) {
   const double q5 = (tau * tn + tn * tn) * om - tn * dtf * edt;
   // compression factor of this Gauss point (interior faces only), 1/p = l2 / rho
   double alpha = 1.0;
-  if (!bnd) {
+  if (!bnd && ph.cf) {
     const double icl = rsqrt_hd(ph.gamma * gl.h), icr = rsqrt_hd(ph.gamma * gr.h);
     const double dp = fabs(gl.p - gr.p);
     const double dn = gl.U * icl - gr.U * icr, d1 = gl.V * icl - gr.V * icr, d2 = gl.W * icl - gr.W * icr;

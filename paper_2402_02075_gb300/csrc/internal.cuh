@@ -36,7 +36,7 @@ __host__ __device__ __forceinline__ void set_err(DevErr* e, int code, int index,
 // constants of the physical model passed by value to the kernels
 struct Phys {
   double gamma, K, mu, prandtl, eps_inviscid, c_press, weno_eps, cfl_fine, cfl_coarse, suth;
-  int viscous, dt_mode;
+  int viscous, dt_mode, cf;
   double Winf[5];
 };
 

@@ -79,6 +79,7 @@ def _state(mesh, nc, kind, mach=0.5):
     ("periodic6", "noise", dict(mach=0.5, viscous=1, reynolds=200.0, prandtl=0.72)),
     ("wall", "noise", dict(mach=0.5, viscous=1, reynolds=1e4, prandtl=0.72)),
     ("wall", "noise", dict(mach=0.5, viscous=1, reynolds=1e4, prandtl=0.72, sutherland=110.4 / 288.15)),
+    ("wall", "noise", dict(mach=0.5, viscous=1, reynolds=1e4, prandtl=0.72, compression_factor=0)),
     ("ramp", "noise", dict(mach=3.0)),
     ("scale8", "noise", dict(mach=0.8, viscous=1, reynolds=1e5, prandtl=0.72)),
 ])

@@ -221,7 +221,7 @@ def test_vcycles_with_lusgs_coarse_smoother(cg, orc, case):
 
 
 @pytest.mark.parametrize("extra", [dict(correction_relax=0.5), dict(prolongation=1),
-                                   dict(prolongation=1, correction_relax=0.7)])
+                                   dict(prolongation=1, correction_relax=0.7), dict(compression_factor=0)])
 def test_vcycles_with_relaxed_or_smoothed_correction(cg, orc, extra):
     """correction_relax r < 1 scales the injected coarse correction and prolongation 1 averages it
     over face neighbours, on every level, the same way in the oracle."""

@@ -166,3 +166,16 @@ def test_zero_area_coarse_face_carries_no_flux(orc):
     before = Wf @ vol
     S.run(2, multigrid=True)
     np.testing.assert_allclose(S.state()[0] @ vol, before, rtol=1e-13, atol=1e-15)
+
+
+def test_compression_factor_off_gives_alpha_one(orc):
+    """compression_factor = 0: every Gauss-point factor, hence every cell's alpha, is exactly 1."""
+    M = orc.Mesh(mg.periodic_box(6))
+    S = orc.Solver(M, orc.params(mach=0.5, compression_factor=0))
+    rng = np.random.default_rng(3)
+    W, G = mg.uniform_state(M.nc, mach=0.5)
+    S.set_state(W * (1 + 0.05 * rng.standard_normal(W.shape)), 0.1 * rng.standard_normal(G.shape))
+    assert np.all(S.residual()["alpha"] == 1.0)
+    S1 = orc.Solver(M, orc.params(mach=0.5))
+    S1.set_state(*S.state()[:2])
+    assert np.any(S1.residual()["alpha"] < 1.0)
