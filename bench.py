@@ -236,6 +236,45 @@ def run_converge(cg, torch, slab):
             "iterations)", "cases": out}
 
 
+def run_scale(args):
+    """Scale sweep: quadrant-layout boxes of 1.0 M, 5.0 M and 20.0 M cells (hex / prism / tet
+    quadrants, no-slip wall, M 0.8, Re 1e5), single-grid FP64 steps, FP64 V-cycles and mixed
+    V-cycles, Mcell-iters/s from CUDA events over `steps` iterations after `warmup`."""
+    import torch
+    import meshgen as mg
+    import paper_2402_02075_gb300 as cg
+    phys = dict(mach=0.8, reynolds=1e5, prandtl=0.72, viscous=1, n_levels=3)
+    rows = []
+    for n in (84, 144, 228):
+        t0 = time.perf_counter()
+        mesh = mg.scale_box(n)
+        ctx = cg.upload_mesh(mesh, cg.default_params(**phys))
+        setup = time.perf_counter() - t0
+        W, G = mg.uniform_state(ctx.nc, mach=0.8)
+        Wd, Gd = torch.from_numpy(W).cuda(), torch.from_numpy(G).cuda()
+        row = {"n": n, "cells": ctx.nc, "setup_s": setup}
+        for key, mgrid, prec in (("single_grid_fp64", False, 0), ("vcycle_fp64", True, 0), ("vcycle_mixed", True, 1)):
+            ctx.set_params(cg.default_params(precision=prec, **phys))
+            ctx.state_init(Wd, Gd)
+            run = ctx.vcycle if mgrid else ctx.step
+            run(args.warmup, history=False)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(ctx.stream)
+            run(args.steps, history=False)
+            e1.record(ctx.stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            row[key] = {"ms_per_iter": ms, "Mcell_iters_per_s": ctx.nc / (ms * 1e-3) / 1e6}
+        rows.append(row)
+        ctx.close()
+        del mesh, Wd, Gd
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "data": "synthetic (seeded quadrant-layout boxes, free-stream start)", "dtype": "f64",
+                      "scale": rows}))
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -277,8 +316,13 @@ def main():
     ap.add_argument("--no-converge", action="store_true")
     ap.add_argument("--size", default="full", choices=["full", "small"],
                     help="small: the same layout at 48x32x32 (profiling captures only)")
+    ap.add_argument("--scale", action="store_true",
+                    help="scale sweep at 1.0M / 5.0M / 20.0M cells instead of the benchmark line")
     args = ap.parse_args()
     global WORKLOAD
+    if args.scale:
+        run_scale(args)
+        return
     if args.size == "small":
         WORKLOAD = dict(nx=48, ny=32, nz=32)
     if args.impl == "reference":
