@@ -25,11 +25,11 @@ from __future__ import annotations
 
 import numpy as np
 
-TET, PRISM, HEX = 4, 5, 6
+TET, PRISM, HEX, PYRAMID = 4, 5, 6, 7
 BC_SLIP, BC_NOSLIP, BC_FARFIELD, BC_SUPER_IN, BC_SUPER_OUT = 1, 2, 3, 4, 5
 PERIODIC_TAG0 = 100
 
-_HEX, _PRZ, _PRX, _TET = 0, 1, 2, 3  # grid-cell split kinds
+_HEX, _PRZ, _PRX, _TET, _PYR = 0, 1, 2, 3, 4  # grid-cell split kinds
 
 
 def splitmix64(x):
@@ -59,7 +59,9 @@ def box_mesh(nx, ny, nz, split, xs=None, ys=None, zs=None, periodic=(False, Fals
              bc=None, jitter=0.0, seed=2402, jitter_mask=None, mapping=None):
     """Mixed-element mesh of a structured box.
 
-    split(i, j, k) -> int array of grid-cell kinds (0 hex, 1 prism_z, 2 prism_x, 3 Kuhn tets),
+    split(i, j, k) -> int array of grid-cell kinds (0 hex, 1 prism_z, 2 prism_x, 3 Kuhn tets,
+    4 six pyramids on the faces of the cell with a new apex node at its node mean: all faces of the
+    grid cell stay quadrilaterals, so pyramid cells border hexahedra or the boundary),
     evaluated on index arrays.  xs/ys/zs are the grid-line coordinates (default [0,1]).
     bc maps 'xmin','xmax','ymin','ymax','zmin','zmax' to a tag for non-periodic sides.
     jitter is the +-fraction of the local spacing applied per coordinate; boundary nodes
@@ -115,9 +117,8 @@ def box_mesh(nx, ny, nz, split, xs=None, ys=None, zs=None, periodic=(False, Fals
         for b in (0, 1):
             for cc in (0, 1):
                 c[(a, b, cc)] = nid(gi + a, gj + b, gk + cc)
-    nsub = np.array([1, 2, 2, 6])[kind]
-    nper = np.array([8, 12, 12, 24])[kind]  # node entries per grid cell
-    sub_types = {_HEX: [HEX], _PRZ: [PRISM, PRISM], _PRX: [PRISM, PRISM], _TET: [TET] * 6}
+    nsub = np.array([1, 2, 2, 6, 6])[kind]
+    sub_types = {_HEX: [HEX], _PRZ: [PRISM, PRISM], _PRX: [PRISM, PRISM], _TET: [TET] * 6, _PYR: [PYRAMID] * 6}
     blocks = {}
     blocks[_HEX] = [[c[0, 0, 0], c[1, 0, 0], c[1, 1, 0], c[0, 1, 0], c[0, 0, 1], c[1, 0, 1], c[1, 1, 1], c[0, 1, 1]]]
     blocks[_PRZ] = [[c[0, 0, 0], c[1, 0, 0], c[1, 1, 0], c[0, 0, 1], c[1, 0, 1], c[1, 1, 1]],
@@ -135,25 +136,35 @@ def box_mesh(nx, ny, nz, split, xs=None, ys=None, zs=None, periodic=(False, Fals
         verts = [p0, p1, p2, p3] if sign > 0 else [p0, p2, p1, p3]
         tets.append([c[v] for v in verts])
     blocks[_TET] = tets
+    # pyramids: apex nodes appended after the grid nodes, one per pyramid grid cell (node mean)
+    pyr = np.nonzero(kind == _PYR)[0]
+    apex = np.zeros(len(kind), dtype=np.int64)
+    if len(pyr):
+        corners = np.stack([c[v][pyr] for v in c], axis=1)  # [m][8]
+        apex[pyr] = len(xyz) + np.arange(len(pyr))
+        xyz = np.concatenate([xyz, xyz[corners].mean(axis=1)])
+    hexv = [c[0, 0, 0], c[1, 0, 0], c[1, 1, 0], c[0, 1, 0], c[0, 0, 1], c[1, 0, 1], c[1, 1, 1], c[0, 1, 1]]
+    # base = the grid cell's outward face reversed (counter-clockwise seen from the apex), then apex
+    blocks[_PYR] = [[hexv[i] for i in f] + [apex] for f in ((1, 2, 3, 0), (7, 6, 5, 4), (4, 5, 1, 0),
+                                                            (5, 6, 2, 1), (6, 7, 3, 2), (7, 4, 0, 3))]
 
     ncell = int(nsub.sum())
     cell_type = np.empty(ncell, dtype=np.int8)
     counts = np.empty(ncell, dtype=np.int64)
     first_cell = np.concatenate([[0], np.cumsum(nsub)[:-1]])
-    for kd in (_HEX, _PRZ, _PRX, _TET):
+    for kd in (_HEX, _PRZ, _PRX, _TET, _PYR):
         sel = np.nonzero(kind == kd)[0]
         for s, t in enumerate(sub_types[kd]):
             cell_type[first_cell[sel] + s] = t
-            counts[first_cell[sel] + s] = {TET: 4, PRISM: 6, HEX: 8}[t]
+            counts[first_cell[sel] + s] = {TET: 4, PRISM: 6, HEX: 8, PYRAMID: 5}[t]
     cell_ptr = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
     cell_nodes = np.empty(cell_ptr[-1], dtype=np.int32)
-    for kd in (_HEX, _PRZ, _PRX, _TET):
+    for kd in (_HEX, _PRZ, _PRX, _TET, _PYR):
         sel = np.nonzero(kind == kd)[0]
         for s, nodes in enumerate(blocks[kd]):
             start = cell_ptr[first_cell[sel] + s]
             for q, arr in enumerate(nodes):
                 cell_nodes[start + q] = arr[sel]
-    del nper
 
     # ---- boundary faces ----------------------------------------------------------------------
     tri_x = np.isin(kind, (_PRX, _TET))
@@ -306,6 +317,18 @@ def wall_box(nx=96, ny=64, nz=64, n_prism=None, first=1e-4, ratio=1.1, jitter=0.
                     bc=dict(xmin=BC_FARFIELD, xmax=BC_FARFIELD, zmin=BC_NOSLIP, zmax=BC_FARFIELD),
                     jitter=jitter, seed=seed,
                     jitter_mask=(lambda i, j, k: k > n_prism) if jitter > 0 else None)
+
+
+def pyramid_box(n=6, jitter=0.05, seed=2402, periodic=True):
+    """Box of hexahedra with a central block of pyramid-split cells (six pyramids per grid cell around
+    a node-mean apex); periodic, or farfield on every side."""
+    lo, hi = n // 3, n - n // 3
+
+    def split(i, j, k):
+        inside = (i >= lo) & (i < hi) & (j >= lo) & (j < hi) & (k >= lo) & (k < hi)
+        return np.where(inside, _PYR, _HEX)
+    bc = None if periodic else {k: BC_FARFIELD for k in ("xmin", "xmax", "ymin", "ymax", "zmin", "zmax")}
+    return box_mesh(n, n, n, split, periodic=(periodic,) * 3, bc=bc, jitter=jitter, seed=seed)
 
 
 def prism_slab(nx=32, ny=4, nz=24, first=1e-3, ratio=1.2, periodic=False):

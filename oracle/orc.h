@@ -42,7 +42,7 @@ typedef struct {
 typedef struct {
   /* fine mesh */
   int64_t n_nodes, nc, nf, n_int, n_per, n_bnd;
-  int8_t *ctype;                 /* 4 tet, 5 prism, 6 hex (= number of faces) */
+  int8_t *ctype;                 /* 4 tet, 5 prism, 6 hex, 7 pyramid (orc_nfaces: number of faces) */
   double *vol, *ctr, *m2;        /* [nc], [nc][3], [nc][6] central second-moment averages xx,yy,zz,xy,yz,xz */
   /* geometry of the coarsening (orc_mesh.c canon_face): [nc], [nc][3], [nf][3], [nf], [nf][3] */
   double *cvol, *cctr, *cSn, *carea, *camom;
@@ -98,6 +98,7 @@ int orc_lusgs_step(const orc_params* P, const orc_level* L, const int32_t* color
                    const double* RHS, const double* dt, int64_t* skipped);
 
 /* mesh (orc_mesh.c) */
+int orc_nfaces(int t);
 int orc_mesh_build(orc_mesh* M, int64_t n_nodes, const double* xyz, int64_t n_cells, const int8_t* ctype,
                    const int64_t* cell_ptr, const int32_t* cell_nodes, int64_t n_bfaces,
                    const int64_t* bface_ptr, const int32_t* bface_nodes, const int32_t* bface_tag,

@@ -23,9 +23,14 @@
 static const int FTET[4][4] = {{0, 2, 1, -1}, {0, 1, 3, -1}, {1, 2, 3, -1}, {0, 3, 2, -1}};
 static const int FPRI[5][4] = {{0, 2, 1, -1}, {3, 4, 5, -1}, {0, 1, 4, 3}, {1, 2, 5, 4}, {2, 0, 3, 5}};
 static const int FHEX[6][4] = {{0, 3, 2, 1}, {4, 5, 6, 7}, {0, 1, 5, 4}, {1, 2, 6, 5}, {2, 3, 7, 6}, {3, 0, 4, 7}};
+/* pyramid (type 7): base 0..3 counter-clockwise seen from the apex 4 */
+static const int FPYR[5][4] = {{0, 3, 2, 1}, {0, 1, 4, -1}, {1, 2, 4, -1}, {2, 3, 4, -1}, {3, 0, 4, -1}};
+
+/* faces of a cell type: 4 tetrahedron, 5 prism, 6 hexahedron, 7 pyramid (5) */
+int orc_nfaces(int t) { return t == 7 ? 5 : t; }
 
 static int local_face(int t, int lf, const int32_t* cn, int32_t out[4]) {
-  const int* f = t == 4 ? FTET[lf] : (t == 5 ? FPRI[lf] : FHEX[lf]);
+  const int* f = t == 4 ? FTET[lf] : (t == 5 ? FPRI[lf] : (t == 7 ? FPYR[lf] : FHEX[lf]));
   int nv = f[3] < 0 ? 3 : 4;
   for (int i = 0; i < nv; ++i) out[i] = cn[f[i]];
   return nv;
@@ -146,6 +151,16 @@ static double det3(const double a[3], const double b[3], const double c[3]) {
 
 /* volume, centroid and central second-moment averages of one cell */
 static void cell_geom(int t, const double* X, double* vol, double c[3], double m2[6]) {
+  if (t == 7) { /* pyramid: the hexahedron map with its top face collapsed onto the apex */
+    double H[24];
+    for (int i = 0; i < 4; ++i)
+      for (int d = 0; d < 3; ++d) {
+        H[3 * i + d] = X[3 * i + d];
+        H[3 * (i + 4) + d] = X[12 + d];
+      }
+    cell_geom(6, H, vol, c, m2);
+    return;
+  }
   if (t == 4) {
     double e1[3], e2[3], e3[3];
     for (int d = 0; d < 3; ++d) {
@@ -274,17 +289,17 @@ int orc_mesh_build(orc_mesh* M, int64_t n_nodes, const double* xyz, int64_t n_ce
   for (int64_t c = 0; c < n_cells; ++c) {
     int t = ctype[c];
     int64_t cnt = cell_ptr[c + 1] - cell_ptr[c];
-    if (!((t == 4 && cnt == 4) || (t == 5 && cnt == 6) || (t == 6 && cnt == 8)))
+    if (!((t == 4 && cnt == 4) || (t == 5 && cnt == 6) || (t == 6 && cnt == 8) || (t == 7 && cnt == 5)))
       FAIL("cell %lld: bad type/node count", (long long)c);
     for (int64_t q = cell_ptr[c]; q < cell_ptr[c + 1]; ++q)
       if (cell_nodes[q] < 0 || cell_nodes[q] >= n_nodes) FAIL("cell %lld: node out of range", (long long)c);
-    nrec += t;
+    nrec += orc_nfaces(t);
   }
   recs = malloc(sizeof(cfrec) * (nrec ? nrec : 1));
   {
     int64_t r = 0;
     for (int64_t c = 0; c < n_cells; ++c)
-      for (int lf = 0; lf < ctype[c]; ++lf) {
+      for (int lf = 0; lf < orc_nfaces(ctype[c]); ++lf) {
         int32_t nodes[4];
         int nv = local_face(ctype[c], lf, cell_nodes + cell_ptr[c], nodes);
         make_key(nodes, nv, recs[r].key);
@@ -478,7 +493,7 @@ int orc_mesh_build(orc_mesh* M, int64_t n_nodes, const double* xyz, int64_t n_ce
     }
   }
   for (int64_t c = 0; c < n_cells; ++c)
-    for (int lf = 0; lf < ctype[c]; ++lf)
+    for (int lf = 0; lf < orc_nfaces(ctype[c]); ++lf)
       if (M->cf[6 * c + lf] < 0) FAIL("cell %lld local face %d unassigned", (long long)c, lf);
   /* geometry of the coarsening */
   M->cvol = malloc(sizeof(double) * n_cells);
@@ -494,7 +509,7 @@ int orc_mesh_build(orc_mesh* M, int64_t n_nodes, const double* xyz, int64_t n_ce
       M->cctr[3 * c + d] = a / (double)nn;
     }
     double v = 0.0;
-    for (int lf = 0; lf < ctype[c]; ++lf) {
+    for (int lf = 0; lf < orc_nfaces(ctype[c]); ++lf) {
       int32_t nodes[4];
       int nv = local_face(ctype[c], lf, cell_nodes + cell_ptr[c], nodes);
       double P[12], S[3], X[3];
@@ -604,12 +619,15 @@ int orc_mesh_qpoints(void* mp, const int8_t* ctype, const int64_t* cell_ptr, con
     int nn = (int)(cell_ptr[c + 1] - cell_ptr[c]);
     for (int i = 0; i < nn; ++i)
       for (int d = 0; d < 3; ++d) X[3 * i + d] = xyz[3 * (int64_t)cell_nodes[cell_ptr[c] + i] + d];
+    if (ctype[c] == 7)
+      for (int i = 5; i < 8; ++i)
+        for (int d = 0; d < 3; ++d) X[3 * i + d] = X[12 + d];
     int q = 0;
     for (int a = 0; a < n1d; ++a)
       for (int b = 0; b < n1d; ++b)
         for (int e = 0; e < n1d; ++e, ++q) {
           double x[3] = {0, 0, 0}, j1[3] = {0, 0, 0}, j2[3] = {0, 0, 0}, j3[3] = {0, 0, 0}, w;
-          if (ctype[c] == 6) {
+          if (ctype[c] == 6 || ctype[c] == 7) {
             double xi = gx[a], et = gx[b], ze = gx[e];
             static const int sg[8][3] = {{-1, -1, -1}, {1, -1, -1}, {1, 1, -1}, {-1, 1, -1},
                                          {-1, -1, 1},  {1, -1, 1},  {1, 1, 1},  {-1, 1, 1}};

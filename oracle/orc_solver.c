@@ -81,7 +81,7 @@ static void mirror_m2(const double m[6], const double n[3], double out[6]) {
 
 static int build_stencil(const orc_solver* S, const double* W, const double* G, int64_t i, stencil* st) {
   const orc_mesh* M = S->M;
-  st->nf = M->ctype[i];
+  st->nf = orc_nfaces(M->ctype[i]);
   for (int m = 0; m < st->nf; ++m) {
     int64_t f = M->cf[6 * i + m];
     int side = M->cside[6 * i + m];
@@ -309,7 +309,7 @@ static void local_dt_fine(const orc_solver* S, const double* W, double* dt) {
     double p = (g - 1.0) * (w[4] - 0.5 * rho * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
     double c = sqrt(g * p / rho), nu = S->P.viscous ? orc_viscosity(&S->ph, g * p / rho) / rho : 0.0;
     double sum = 0.0, V = M->vol[i];
-    for (int m = 0; m < M->ctype[i]; ++m) {
+    for (int m = 0; m < orc_nfaces(M->ctype[i]); ++m) {
       int64_t f = M->cf[6 * i + m];
       double Sn[3], area, xc[3];
       face_sum(M, f, Sn, &area, xc);

@@ -40,15 +40,20 @@ def test_unjittered_cell_moments_closed_forms(orc):
     np.testing.assert_allclose(vol, h ** 3 / 6.0, rtol=1e-13)
 
 
-@pytest.mark.parametrize("periodic", [True, False])
-def test_jittered_mixed_mesh_divergence_theorem(orc, periodic):
+NFACES = {4: 4, 5: 5, 6: 6, 7: 5}
+
+
+@pytest.mark.parametrize("kind", ["periodic", "farfield", "pyramids"])
+def test_jittered_mixed_mesh_divergence_theorem(orc, kind):
     """Per cell: sum of outward area vectors = 0, |Omega| = (1/3) sum x.dA and
     int x_d dV = (1/2) sum x_d^2 dA_d (the face rules are exact for these integrands on bilinear
-    faces), so the volume quadrature is pinned by the surface quadrature."""
-    if periodic:
+    faces), so the volume quadrature is pinned by the surface quadrature (pyramids included)."""
+    if kind == "periodic":
         mesh = mg.periodic_box(6)
-    else:
+    elif kind == "farfield":
         mesh = mg.scale_box(6)
+    else:
+        mesh = mg.pyramid_box(6)
     M = orc.Mesh(mesh)
     vol, ctr, m2 = M.cells()
     F = M.faces()
@@ -57,7 +62,7 @@ def test_jittered_mixed_mesh_divergence_theorem(orc, periodic):
     V3 = np.zeros(M.nc)
     C2 = np.zeros((M.nc, 3))
     for i in range(M.nc):
-        for m in range(mesh["cell_type"][i]):
+        for m in range(NFACES[int(mesh["cell_type"][i])]):
             f, side = F["cf"][i, m], F["cside"][i, m]
             k = F["ngp"][f]
             dA = F["gA"][f, :k] * (-1.0 if side else 1.0)
@@ -123,10 +128,11 @@ def _state_from(fields):
     return W, G
 
 
-def test_p2_reproduces_quadratic_fields(orc):
+@pytest.mark.parametrize("kind", ["mixed", "pyramids"])
+def test_p2_reproduces_quadratic_fields(orc, kind):
     """The constrained least-squares p^2 (Sec. 3.1) is exact for quadratic data on the jittered
-    mixed mesh (cells whose stencil has no boundary face)."""
-    mesh = mg.scale_box(7)
+    mixed mesh and on a box with pyramids (cells whose stencil has no boundary face)."""
+    mesh = mg.scale_box(7) if kind == "mixed" else mg.pyramid_box(7, periodic=False)
     M = orc.Mesh(mesh)
     S = orc.Solver(M, orc.params(mach=0.2, n_levels=1))
     rng = np.random.default_rng(0)
@@ -217,3 +223,21 @@ def test_coarsening_geometry(orc):
     inner = F["fR"] >= 0
     np.add.at(clos, F["fR"][inner], -Sn[inner])
     assert np.abs(clos).max() < 1e-15
+
+
+def test_pyramid_closed_forms(orc):
+    """Unjittered pyramids (six per grid cell of side h around its centre): volume h^3/6, centroid a
+    quarter of the way from the base centre to the apex, and the canonical coarsening volume equal."""
+    n = 6
+    h = 1.0 / n
+    mesh = mg.pyramid_box(n, jitter=0.0)
+    M = orc.Mesh(mesh)
+    vol, ctr, _ = M.cells()
+    pyr = np.nonzero(np.asarray(mesh["cell_type"]) == 7)[0]
+    assert len(pyr) == 6 * (n - 2 * (n // 3)) ** 3
+    np.testing.assert_allclose(vol[pyr], h ** 3 / 6.0, rtol=1e-13)
+    X = mesh["xyz"][mesh["cell_nodes"][mesh["cell_ptr"][pyr][:, None] + np.arange(5)]]
+    base = X[:, :4].mean(axis=1)
+    np.testing.assert_allclose(ctr[pyr], base + 0.25 * (X[:, 4] - base), rtol=0, atol=1e-15)
+    cvol = M.coarsening_geometry()[0]
+    np.testing.assert_allclose(cvol[pyr], h ** 3 / 6.0, rtol=1e-13)

@@ -179,3 +179,12 @@ def test_compression_factor_off_gives_alpha_one(orc):
     S1 = orc.Solver(M, orc.params(mach=0.5))
     S1.set_state(*S.state()[:2])
     assert np.any(S1.residual()["alpha"] < 1.0)
+
+
+def test_free_stream_preserved_with_pyramids(orc):
+    M, S, W = _uniform(orc, mg.pyramid_box(6), mach=0.3, aoa=(15.0, 5.0), viscous=1, reynolds=100.0)
+    vol, _, _ = M.cells()
+    r = S.residual()
+    assert np.abs(r["res"] / vol).max() < 1e-11
+    S.run(2, multigrid=True)
+    np.testing.assert_allclose(S.state()[0], W, rtol=0, atol=1e-13)
