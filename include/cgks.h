@@ -1,5 +1,5 @@
 /* cgks.h - C ABI of libcgks, a GB300 (sm_103a) implementation of the multigrid compact gas-kinetic
- * scheme (CGKS) for steady flows on 3D mixed hexahedral/prismatic/tetrahedral meshes
+ * scheme (CGKS) for steady flows on 3D mixed hexahedral/prismatic/pyramidal/tetrahedral meshes
  * (H. Liu, X. Ji, Y. Mao, Y. Ding, K. Xu, arXiv:2402.02075).
  *
  * Conventions shared by every entry point
@@ -98,8 +98,9 @@ cgks_status cgks_set_params(cgks_ctx* ctx, const cgks_params* params);
  * Gauss points (3 per triangle, 4 per quadrilateral, Sec. 2.2), cell volume moments, the
  * reconstruction operators (Sec. 3) and the coarse levels by hash agglomeration (Sec. 4.1).
  *   xyz         double[n_nodes][3]
- *   cell_type   int8[n_cells]: 4 tetrahedron, 5 prism, 6 hexahedron; nodes in VTK order
- *   cell_ptr    int64[n_cells + 1] offsets into cell_nodes (4, 6 or 8 nodes per cell)
+ *   cell_type   int8[n_cells]: 4 tetrahedron, 5 prism, 6 hexahedron, 7 pyramid; nodes in VTK
+ *               order (pyramid: base 0..3 counter-clockwise seen from the apex, apex 4)
+ *   cell_ptr    int64[n_cells + 1] offsets into cell_nodes (4, 6, 8 or 5 nodes per cell)
  *   cell_nodes  int32 node ids
  *   bface_ptr   int64[n_bfaces + 1], bface_nodes int32 (3 or 4 nodes, any order), bface_tag int32
  *   periodic_pairs int32[n_periodic][2] boundary-face ids (nullable when n_periodic == 0); the

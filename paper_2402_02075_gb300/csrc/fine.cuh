@@ -46,7 +46,7 @@ struct ReconArgs {
 
 HD void reconstruct_body(int64_t i, const ReconArgs& a) {
   const int64_t nc = a.nc, nf = a.nf;
-  const int nt = a.ctype[i];
+  const int nt = a.ctype[i] == 7 ? 5 : a.ctype[i];  // faces: pyramids (type 7) have 5
   const Phys& ph = a.ph;
   double Q0[5];
 #pragma unroll
@@ -596,7 +596,7 @@ HD void gather_body(int64_t i, const GatherArgs& a) {
 #pragma unroll
   for (int j = 0; j < 15; ++j) gs[j] = 0.0;
   double al = 1.0;
-  const int nt = a.ctype[i];
+  const int nt = a.ctype[i] == 7 ? 5 : a.ctype[i];  // faces: pyramids (type 7) have 5
   for (int m = 0; m < nt; ++m) {
     const int64_t f = a.cf[(int64_t)m * nc + i];
     const double s = a.cside[(int64_t)m * nc + i] ? -1.0 : 1.0;

@@ -14,12 +14,16 @@
 #include "internal.cuh"
 
 // local faces of each cell type, outward orientation (VTK-like node numbering)
-__constant__ int8_t c_lface[3][6][4] = {
+// (type 4 tetrahedron, 5 prism, 6 hexahedron, 7 pyramid: base 0..3 counter-clockwise seen from apex 4)
+__constant__ int8_t c_lface[4][6][4] = {
     {{0, 2, 1, -1}, {0, 1, 3, -1}, {1, 2, 3, -1}, {0, 3, 2, -1}, {-1, -1, -1, -1}, {-1, -1, -1, -1}},
     {{0, 2, 1, -1}, {3, 4, 5, -1}, {0, 1, 4, 3}, {1, 2, 5, 4}, {2, 0, 3, 5}, {-1, -1, -1, -1}},
-    {{0, 3, 2, 1}, {4, 5, 6, 7}, {0, 1, 5, 4}, {1, 2, 6, 5}, {2, 3, 7, 6}, {3, 0, 4, 7}}};
+    {{0, 3, 2, 1}, {4, 5, 6, 7}, {0, 1, 5, 4}, {1, 2, 6, 5}, {2, 3, 7, 6}, {3, 0, 4, 7}},
+    {{0, 3, 2, 1}, {0, 1, 4, -1}, {1, 2, 4, -1}, {2, 3, 4, -1}, {3, 0, 4, -1}, {-1, -1, -1, -1}}};
 
 __device__ __forceinline__ int lface_nv(int t, int lf) { return c_lface[t - 4][lf][3] < 0 ? 3 : 4; }
+__host__ __device__ __forceinline__ int cell_nfaces(int t) { return t == 7 ? 5 : t; }
+__host__ __device__ __forceinline__ int cell_nnodes(int t) { return t == 4 ? 4 : (t == 5 ? 6 : (t == 7 ? 5 : 8)); }
 
 // ---- geometry of the coarsening ------------------------------------------------------------------
 // The agglomeration decides merges by comparing a skewness measure with a limit, so its geometric
@@ -72,14 +76,14 @@ __global__ void k_canon_cells(int64_t nc, const int8_t* ctype, const int64_t* cp
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= nc) return;
   const int t = ctype[c];
-  const int nn = t == 4 ? 4 : (t == 5 ? 6 : 8);
+  const int nn = cell_nnodes(t);
   for (int d = 0; d < 3; ++d) {
     double a = xyz[3 * (int64_t)cn[cptr[c]] + d];
     for (int i = 1; i < nn; ++i) a = __dadd_rn(a, xyz[3 * (int64_t)cn[cptr[c] + i] + d]);
     ctr[d * nc + c] = __ddiv_rn(a, (double)nn);
   }
   double v = 0.0;
-  for (int lf = 0; lf < t; ++lf) {
+  for (int lf = 0; lf < cell_nfaces(t); ++lf) {
     const int nv = lface_nv(t, lf);
     double P[4][3], S[3], X[3];
     for (int i = 0; i < nv; ++i) {
@@ -141,7 +145,7 @@ __global__ void k_validate_cells(int64_t nc, const int8_t* ctype, const int64_t*
   if (c >= nc) return;
   const int t = ctype[c];
   const int64_t cnt = cptr[c + 1] - cptr[c];
-  if (!((t == 4 && cnt == 4) || (t == 5 && cnt == 6) || (t == 6 && cnt == 8))) {
+  if (!((t == 4 && cnt == 4) || (t == 5 && cnt == 6) || (t == 6 && cnt == 8) || (t == 7 && cnt == 5))) {
     set_err(err, CGKS_EMESH, (int)c, 1);
     return;
   }
@@ -156,7 +160,7 @@ __global__ void k_insert_faces(int64_t nc, const int8_t* ctype, const int64_t* c
   if (r >= nc * 6) return;
   const int64_t c = r / 6;
   const int lf = (int)(r % 6);
-  if (lf >= ctype[c]) return;
+  if (lf >= cell_nfaces(ctype[c])) return;
   const Key4 k = cell_face_key(ctype, cptr, cn, c, lf);
   uint64_t h = key_hash(k) & mask;
   for (uint64_t probe = 0; probe <= mask; ++probe, h = (h + 1) & mask) {
@@ -218,7 +222,7 @@ __global__ void k_check_records(int64_t nc, const int8_t* ctype, const int64_t* 
                                 DevErr* err) {
   int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (r >= nc * 6) return;
-  if ((int)(r % 6) >= ctype[r / 6]) return;
+  if ((int)(r % 6) >= cell_nfaces(ctype[r / 6])) return;
   if (partner[r] < 0 && bnd_of[r] < 0) set_err(err, CGKS_EMESH, (int)(r / 6), 20);
 }
 
@@ -253,7 +257,7 @@ __global__ void k_count_owned(int64_t nc, const int8_t* ctype, const int64_t* pa
   int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= nc) return;
   int n = 0;
-  for (int lf = 0; lf < ctype[c]; ++lf) {
+  for (int lf = 0; lf < cell_nfaces(ctype[c]); ++lf) {
     const int64_t o = partner[c * 6 + lf];
     if (o >= 0 && o / 6 > c) ++n;
   }
@@ -267,7 +271,7 @@ __global__ void k_write_interior(int64_t nc, const int8_t* ctype, const int64_t*
   if (c >= nc) return;
   int64_t nbr[6];
   int lfs[6], n = 0;
-  for (int lf = 0; lf < ctype[c]; ++lf) {
+  for (int lf = 0; lf < cell_nfaces(ctype[c]); ++lf) {
     const int64_t o = partner[c * 6 + lf];
     if (o >= 0 && o / 6 > c) {
       int j = n++;
@@ -429,11 +433,16 @@ __global__ void k_cell_geom(int64_t nc, const int8_t* ctype, const int64_t* cptr
                             double* vol, double* ctr, double* m2, DevErr* err) {
   int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= nc) return;
-  const int t = ctype[c];
+  int t = ctype[c];
   double X[8][3];
-  const int nn = t == 4 ? 4 : (t == 5 ? 6 : 8);
+  const int nn = cell_nnodes(t);
   for (int i = 0; i < nn; ++i)
     for (int d = 0; d < 3; ++d) X[i][d] = xyz[3 * (int64_t)cn[cptr[c] + i] + d];
+  if (t == 7) {  // pyramid: the hexahedron map with its top face collapsed onto the apex
+    for (int i = 5; i < 8; ++i)
+      for (int d = 0; d < 3; ++d) X[i][d] = X[4][d];
+    t = 6;
+  }
   const double q = 0.7745966692414833770;  // sqrt(3/5)
   const double xg[3] = {-q, 0.0, q}, wg[3] = {5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0};
   double V = 0.0, M1[3] = {0, 0, 0}, M2[6] = {0, 0, 0, 0, 0, 0};
@@ -510,7 +519,7 @@ __global__ void k_fill_c2f(int64_t nc, const int8_t* ctype, const int32_t* cf, c
   int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= nc) return;
   int32_t v[6];
-  const int n = ctype[c];
+  const int n = cell_nfaces(ctype[c]);
   for (int m = 0; m < n; ++m) {
     int32_t f = cf[(int64_t)m * nc + c];
     int j = m;
@@ -525,7 +534,7 @@ __global__ void k_fill_c2f(int64_t nc, const int8_t* ctype, const int32_t* cf, c
 
 __global__ void k_types_to_int(int64_t nc, const int8_t* ctype, int32_t* out) {
   int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (c < nc) out[c] = ctype[c];
+  if (c < nc) out[c] = cell_nfaces(ctype[c]);
 }
 
 // ---- dense helpers of the reconstruction-operator precompute (per thread, column-major) --------
@@ -594,7 +603,7 @@ __host__ __device__ void recon_ops_body(int64_t i, const ROArgs& A_) {
                *fctr = A_.fctr, *fnrm = A_.fnrm;
   double *Kop = A_.Kop, *ggw = A_.ggw, *lsw = A_.lsw, *aux = A_.aux, *dtw = A_.dtw;
   DevErr* err = A_.err;
-  const int nt = ctype[i];
+  const int nt = cell_nfaces(ctype[i]);
   const double V = vol[i];
   double c0[3], M0[6];
   for (int d = 0; d < 3; ++d) c0[d] = ctr[d * nc + i];

@@ -39,6 +39,8 @@ MESHES = {
     "wall": lambda: mg.wall_box(12, 8, 12, n_prism=5),
     "ramp": lambda: mg.ramp_box(16, 8, 8, n_prism=3),
     "scale8": lambda: mg.scale_box(8),
+    "pyramid6": lambda: mg.pyramid_box(6),
+    "pyramid6-farfield": lambda: mg.pyramid_box(6, periodic=False),
 }
 
 
@@ -82,6 +84,8 @@ def _state(mesh, nc, kind, mach=0.5):
     ("wall", "noise", dict(mach=0.5, viscous=1, reynolds=1e4, prandtl=0.72, compression_factor=0)),
     ("ramp", "noise", dict(mach=3.0)),
     ("scale8", "noise", dict(mach=0.8, viscous=1, reynolds=1e5, prandtl=0.72)),
+    ("pyramid6", "wave", dict(mach=0.2)),
+    ("pyramid6-farfield", "noise", dict(mach=0.5, viscous=1, reynolds=1e3, prandtl=0.72)),
 ])
 def test_cgks_residual(cg, orc, name, kind, prm):
     mesh = MESHES[name]()
@@ -103,7 +107,7 @@ def test_cgks_residual(cg, orc, name, kind, prm):
     assert abs(r["norm"] - ro["norm"]) <= bound
 
 
-@pytest.mark.parametrize("name", ["periodic6", "wall", "ramp"])
+@pytest.mark.parametrize("name", ["periodic6", "wall", "ramp", "pyramid6-farfield"])
 def test_kfvs_residual_fine_level(cg, orc, name):
     mesh = MESHES[name]()
     ctx, om, os_ = _pair(cg, orc, mesh, n_levels=1, mach=0.5)

@@ -63,6 +63,7 @@ def test_config1_hundred_steps(cg, orc):
     ("wall", lambda: mg.wall_box(16, 8, 16, n_prism=6), 0),
     ("ramp", lambda: mg.ramp_box(24, 12, 8, n_prism=3), 0),
     ("scale10", lambda: mg.scale_box(10), 1),
+    ("pyramid8", lambda: mg.pyramid_box(8), 0),
 ])
 def test_coarsening_is_bit_exact(cg, orc, name, mk, seed):
     mesh = mk()
@@ -103,7 +104,7 @@ def test_coarse_kfvs_residuals(cg, orc, mk):
         assert_normwise(got, ref, 1e-12, f"KFVS residual level {lev}")
 
 
-@pytest.mark.parametrize("case", ["wave", "wall", "ramp", "slab"])
+@pytest.mark.parametrize("case", ["wave", "wall", "ramp", "slab", "pyramid"])
 def test_vcycles(cg, orc, case):
     rng = np.random.default_rng(11)
     if case == "wave":
@@ -120,6 +121,12 @@ def test_vcycles(cg, orc, case):
         mesh = mg.ramp_box(24, 12, 8, n_prism=3)
         W, G = mg.uniform_state(len(mesh["cell_type"]), mach=3.0)
         prm = dict(mach=3.0)
+        n = 3
+    elif case == "pyramid":  # hexahedra around a block of pyramids, farfield on every side
+        mesh = mg.pyramid_box(8, periodic=False)
+        W, G = mg.uniform_state(len(mesh["cell_type"]), mach=0.5)
+        W = W * (1 + 0.01 * rng.standard_normal(W.shape))
+        prm = dict(mach=0.5, viscous=1, reynolds=1e3, prandtl=0.72)
         n = 3
     else:  # a level-2 coarse face of zero net area
         mesh = mg.prism_slab()
