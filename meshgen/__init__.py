@@ -417,3 +417,28 @@ def density_wave_state(mesh, gamma=1.4, mach=0.2, amp=0.01):
         G[1 * 3 + d] = U * drho
         G[4 * 3 + d] = 0.5 * U * U * drho
     return W, G
+
+
+# ---- design perturbations of the compression ramp (inputs of the adjoint checks) ------------------
+
+def ramp_wall_modes(mesh, n_modes=64, angle_deg=15.0, sigma=0.08, depth=0.5, seed=2402):
+    """Node displacement fields [n_modes][n_nodes][3] of the ramp_box wall: mode m moves the nodes
+    normal to the x axis in y by exp(-(x - x_m)^2 / (2 sigma^2)) (x_m seeded uniform in [-0.3, 1.3]),
+    faded linearly to zero at height `depth` above the wall; independent of z, so periodic copies of
+    a node move together."""
+    xyz = mesh["xyz"]
+    rng = np.random.default_rng(seed)
+    xm = rng.uniform(-0.3, 1.3, n_modes)
+    t = np.tan(np.radians(angle_deg))
+    eta = xyz[:, 1] - np.where(xyz[:, 0] > 0.0, xyz[:, 0] * t, 0.0)
+    fade = np.clip(1.0 - eta / depth, 0.0, 1.0)
+    out = np.zeros((n_modes, len(xyz), 3))
+    out[:, :, 1] = np.exp(-(xyz[None, :, 0] - xm[:, None]) ** 2 / (2.0 * sigma ** 2)) * fade[None, :]
+    return out
+
+
+def displaced(mesh, field, eps):
+    """Copy of a mesh dict with its nodes moved by eps * field ([n_nodes][3])."""
+    out = dict(mesh)
+    out["xyz"] = np.ascontiguousarray(mesh["xyz"] + eps * field)
+    return out
