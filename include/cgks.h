@@ -187,9 +187,52 @@ cgks_status cgks_coarse_colors(cgks_ctx* ctx, int level, int32_t* colors, int32_
  * through the start-up transient).  Synchronises. */
 cgks_status cgks_skipped_updates(cgks_ctx* ctx, int64_t* count);
 
-/* Discrete adjoint of the residual (extension, not in the paper).  Returns CGKS_EUNSUPPORTED. */
-cgks_status cgks_adjoint(cgks_ctx* ctx, const double* wall_disp_modes, int n_modes, double* dJ_dmodes,
-                         double* dJ_dmach);
+/* ---- Discrete adjoint of the steady problem (an extension: the paper solves, it does not
+ * differentiate).  The steady compact scheme (Sec. 2.4, 4) has u = (W [5][N], grad W [15][N]) as
+ * unknowns and F(u) = (Res(W, G), Gnew(W, G) - G) = 0, with Res the residual of the explicit update
+ * and Gnew the Gauss-Green gradient.  For a functional J(u, beta) and parameters beta (the free-stream
+ * Mach number, node displacement modes) the adjoint gives dJ/dbeta = dJ/dbeta|_u + lambda^T
+ * dF/dbeta|_u with (dF/du)^T lambda = -(dJ/du)^T.  All calls need compression_factor = 0 (the
+ * factor's pressure-jump terms are not differentiable where the jump vanishes) and dt_mode = 0
+ * (CGKS_EUNSUPPORTED otherwise).  Vectors of 20 rows are [20][N]: the 5 rows of W then the 15 of
+ * grad W, in the layouts of cgks_state_init. */
+
+/* Forms and stores the linearisation of (Res, Gnew) at the current state by forward-mode duals
+ * (41 x 10 doubles per Gauss point, 140 x 51 per cell; device memory owned by the context, freed with
+ * the mesh).  Errors: CGKS_EINVAL (no state), CGKS_ENOMEM, CGKS_EUNSUPPORTED. */
+cgks_status cgks_linearize(cgks_ctx* ctx);
+
+/* Transposed product with the stored linearisation: (W_bar, G_bar) = (d(Res, Gnew)/d(W, G))^T
+ * (res_bar, grad_bar).  res_bar [5][N], grad_bar [15][N] in; W_bar [5][N], G_bar [15][N] out (device
+ * or pinned host, caller-owned).  Errors: CGKS_EINVAL (NULL array, no linearisation). */
+cgks_status cgks_residual_vjp(cgks_ctx* ctx, const double* res_bar, const double* grad_bar, double* W_bar,
+                              double* G_bar);
+
+/* Wall force J = sum over wall faces (tags 1, 2) of p(W) S_component, p the pressure of the wall
+ * cell's average and S the face's area vector (outward from the cell).  J: host scalar out;
+ * dJ_dW: NULLable device [5][N] out (dJ/dW, zero away from the wall).  Synchronises. */
+cgks_status cgks_wall_force(cgks_ctx* ctx, int component, double* J, double* dJ_dW);
+
+/* Solves (dF/du)^T lambda = -dJ_du with the stored linearisation by the transposed pseudo-time
+ * iteration of the explicit scheme: mu <- mu + (dF/du)^T P mu + dJ_du, lambda = P mu, P the local
+ * time steps over the volumes on the W rows (the iteration matrix is the transpose of the explicit
+ * scheme's, so it converges where the scheme does).  dJ_du [20][N] in, lambda [20][N] out (device).
+ * Stops when |(dF/du)^T lambda + dJ_du| <= tol |dJ_du| (checked every 25 iterations) or after
+ * max_iters; iters and rel_res (NULLable host) report the count and the ratio.  Errors:
+ * CGKS_ENOTCONV (tolerance not reached; lambda holds the last iterate), CGKS_ENAN (divergence). */
+cgks_status cgks_adjoint_solve(cgks_ctx* ctx, const double* dJ_du, int64_t max_iters, double tol, double* lambda,
+                               int64_t* iters, double* rel_res);
+
+/* Gradient of the wall force (component 0..2) at the current (steady) state with respect to the
+ * free-stream Mach number and to n_modes node displacement modes: node_modes host
+ * [n_modes][n_nodes][3] (the upload's node order; NULL when n_modes == 0), dJ_dmodes host [n_modes]
+ * out, dJ_dmach host out.  Linearises, solves the adjoint (max_iters, tol as cgks_adjoint_solve),
+ * and takes the parameter partials dF/dbeta, dJ/dbeta at the frozen state by central differences of
+ * the residual with steps h_mach and h_mode (for a mode: the mesh re-uploaded with its nodes moved,
+ * into a one-level context on the same stream).  Synchronises. */
+cgks_status cgks_adjoint(cgks_ctx* ctx, int component, const double* node_modes, int n_modes, double h_mode,
+                         double h_mach, int64_t max_iters, double tol, double* dJ_dmodes, double* dJ_dmach,
+                         int64_t* iters, double* rel_res);
 
 /* Measured FP64 fused-multiply-add throughput of the current device in TFLOP/s (host output),
  * from a register-resident FMA chain kernel; the roofline denominator of the FP64-bound kernels. */

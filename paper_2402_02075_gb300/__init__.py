@@ -24,7 +24,8 @@ STATUS = {0: "CGKS_OK", 1: "CGKS_EINVAL", 2: "CGKS_ENOMEM", 3: "CGKS_ECUDA", 4: 
 EXPORTS = ["cgks_default_params", "cgks_create", "cgks_destroy", "cgks_set_params", "cgks_mesh_upload",
            "cgks_level_info", "cgks_coarse_map", "cgks_level_geometry", "cgks_fine_moments", "cgks_state_init",
            "cgks_state_get", "cgks_residual", "cgks_kfvs_residual", "cgks_kfvs_jvp", "cgks_step", "cgks_vcycle", "cgks_steady_solve",
-           "cgks_coarse_colors", "cgks_skipped_updates", "cgks_adjoint", "cgks_fp64_peak", "cgks_profile", "cgks_kernel_stats", "cgks_density_norm_noalloc",
+           "cgks_coarse_colors", "cgks_skipped_updates", "cgks_linearize", "cgks_residual_vjp",
+           "cgks_wall_force", "cgks_adjoint_solve", "cgks_adjoint", "cgks_fp64_peak", "cgks_profile", "cgks_kernel_stats", "cgks_density_norm_noalloc",
            "cgks_last_error"]
 
 
@@ -73,7 +74,12 @@ def load(path: str = LIB_PATH):
                                   C.POINTER(C.c_double)],
             "cgks_coarse_colors": [P, C.c_int, i32, C.POINTER(C.c_int32)],
             "cgks_skipped_updates": [P, C.POINTER(C.c_int64)],
-            "cgks_adjoint": [P, d, C.c_int, d, d],
+            "cgks_linearize": [P],
+            "cgks_residual_vjp": [P, d, d, d, d],
+            "cgks_wall_force": [P, C.c_int, C.POINTER(C.c_double), d],
+            "cgks_adjoint_solve": [P, d, C.c_int64, C.c_double, d, C.POINTER(C.c_int64), C.POINTER(C.c_double)],
+            "cgks_adjoint": [P, C.c_int, d, C.c_int, C.c_double, C.c_double, C.c_int64, C.c_double, d,
+                             C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double)],
             "cgks_fp64_peak": [C.POINTER(C.c_double)],
             "cgks_profile": [P, C.c_int],
             "cgks_kernel_stats": [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)],
@@ -256,6 +262,41 @@ class Context:
         _check(load().cgks_kernel_stats(self.h, which, C.byref(ms), C.byref(n)), self.h)
         return ms.value, n.value
 
+    # ---- adjoint of the steady problem (compression_factor 0) ----
+    def linearize(self):
+        _check(load().cgks_linearize(self.h), self.h)
+
+    def residual_vjp(self, res_bar, grad_bar):
+        """(W_bar, G_bar) = J^T (res_bar, grad_bar) with the stored linearisation of (Res, Gnew)."""
+        Wb, Gb = self._empty(5, self.nc), self._empty(15, self.nc)
+        _check(load().cgks_residual_vjp(self.h, _ptr(res_bar), _ptr(grad_bar), _ptr(Wb), _ptr(Gb)), self.h)
+        return Wb, Gb
+
+    def wall_force(self, component=1, grad=False):
+        J = C.c_double()
+        dJ = self.torch.zeros(5, self.nc, dtype=self.torch.float64, device="cuda") if grad else None
+        _check(load().cgks_wall_force(self.h, component, C.byref(J), _ptr(dJ)), self.h)
+        return (J.value, dJ) if grad else J.value
+
+    def adjoint_solve(self, dJ_du, max_iters=100000, tol=1e-10):
+        lam = self._empty(20, self.nc)
+        it, rr = C.c_int64(), C.c_double()
+        _check(load().cgks_adjoint_solve(self.h, _ptr(dJ_du), max_iters, tol, _ptr(lam), C.byref(it), C.byref(rr)),
+               self.h)
+        return lam, it.value, rr.value
+
+    def adjoint(self, component=1, modes=None, h_mode=1e-6, h_mach=1e-6, max_iters=100000, tol=1e-10):
+        """dJ/dMach and dJ/d(mode amplitudes) of the wall force at the current steady state; modes:
+        host float64 [n_modes][n_nodes][3] or None."""
+        n = 0 if modes is None else len(modes)
+        md = None if modes is None else np.ascontiguousarray(modes, dtype=np.float64)
+        out = np.zeros(max(n, 1))
+        dm, it, rr = C.c_double(), C.c_int64(), C.c_double()
+        _check(load().cgks_adjoint(self.h, component, None if md is None else md.ctypes.data_as(C.c_void_p), n, h_mode,
+                                   h_mach, max_iters, tol, out.ctypes.data_as(C.c_void_p), C.byref(dm), C.byref(it),
+                                   C.byref(rr)), self.h)
+        return dict(dJ_dmach=dm.value, dJ_dmodes=out[:n], iters=it.value, rel_res=rr.value)
+
     def steady_solve(self, multigrid=True, drop=1e-10, max_iters=100000, raise_on_notconv=True):
         it, fd, sec = C.c_int64(), C.c_double(), C.c_double()
         s = load().cgks_steady_solve(self.h, int(bool(multigrid)), drop, max_iters, C.byref(it), C.byref(fd), C.byref(sec))
@@ -269,3 +310,27 @@ def upload_mesh(mesh, params=None):
     ctx = Context(params)
     ctx.mesh_upload(mesh)
     return ctx
+
+
+def wall_force_function(ctx: Context, modes=None, component=1, **adjoint_kw):
+    """The wall force of the steady state that `ctx` holds as a torch function f(mach, amps) ->
+    J whose backward is the discrete adjoint (cgks_adjoint).  The state is the steady solution at the
+    context's Mach number with the mode amplitudes at zero, so f is evaluated and differentiated
+    there only: mach must equal that Mach number and amps be zero."""
+    import torch
+
+    class _WallForce(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, mach, amps):
+            assert abs(float(mach) - ctx.params.mach) <= 1e-15 * max(1.0, ctx.params.mach)
+            assert amps.numel() == (0 if modes is None else len(modes)) and not bool(torch.any(amps != 0))
+            return torch.tensor(ctx.wall_force(component), dtype=torch.float64)
+
+        @staticmethod
+        def backward(fctx, gout):
+            g = ctx.adjoint(component, modes, **adjoint_kw)
+            s = float(gout)
+            return (torch.tensor(s * g["dJ_dmach"], dtype=torch.float64),
+                    torch.as_tensor(s * g["dJ_dmodes"], dtype=torch.float64))
+
+    return _WallForce.apply

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libcgks.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["api.cu", "mesh.cu", "agglo.cu", "fine.cu", "coarse.cu", "lusgs.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "mesh.cu", "agglo.cu", "fine.cu", "coarse.cu", "lusgs.cu", "noalloc.cu", "adjoint.cu"]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]

@@ -345,6 +345,15 @@ cgks_status cgks_mesh_upload(cgks_ctx* ctx, int64_t n_nodes, const double* xyz, 
   ctx->C.clear();
   ctx->has_mesh = ctx->has_state = false;
   static const int64_t empty64 = 0;
+  ctx->linearized = false;
+  ctx->h_xyz.assign(xyz, xyz + 3 * n_nodes);
+  ctx->h_ctype.assign(cell_type, cell_type + n_cells);
+  ctx->h_cptr.assign(cell_ptr, cell_ptr + n_cells + 1);
+  ctx->h_cnodes.assign(cell_nodes, cell_nodes + cell_ptr[n_cells]);
+  ctx->h_bptr.assign(n_bfaces ? bface_ptr : nullptr, n_bfaces ? bface_ptr + n_bfaces + 1 : nullptr);
+  ctx->h_bnodes.assign(n_bfaces ? bface_nodes : nullptr, n_bfaces ? bface_nodes + bface_ptr[n_bfaces] : nullptr);
+  ctx->h_btag.assign(n_bfaces ? bface_tag : nullptr, n_bfaces ? bface_tag + n_bfaces : nullptr);
+  ctx->h_pairs.assign(n_periodic ? periodic_pairs : nullptr, n_periodic ? periodic_pairs + 2 * n_periodic : nullptr);
   CKS(build_fine_mesh(ctx, n_nodes, xyz, n_cells, cell_type, cell_ptr, cell_nodes, n_bfaces,
                       n_bfaces ? bface_ptr : &empty64, bface_nodes, bface_tag, periodic_pairs, n_periodic));
   CKS(build_levels(ctx));
@@ -575,9 +584,6 @@ cgks_status cgks_skipped_updates(cgks_ctx* ctx, int64_t* count) {
   return CGKS_OK;
 }
 
-cgks_status cgks_adjoint(cgks_ctx* ctx, const double*, int, double*, double*) {
-  return cgks_fail(ctx, CGKS_EUNSUPPORTED, "cgks_adjoint is not available in this build");
-}
 
 __global__ void k_fma_chain(double* out, int iters, double a, double b) {
   double x[8];

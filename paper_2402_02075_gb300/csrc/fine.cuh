@@ -18,6 +18,13 @@
 #include "internal.cuh"
 #include "kinetic.cuh"
 
+// sizes of the stored linearisation (the adjoint): inputs and outputs of one Gauss point, of one
+// cell's reconstruction (7 stencil slots x (W, grad W); the coefficients and the time step)
+#define CGKS_PJ_IN 41
+#define CGKS_PJ_OUT 10
+#define CGKS_RJ_IN 140
+#define CGKS_RJ_OUT 51
+
 HD double rsqrt_hd(double x) {
 #ifdef __CUDA_ARCH__
   return rsqrt(x);
@@ -25,11 +32,16 @@ HD double rsqrt_hd(double x) {
   return 1.0 / sqrt(x);
 #endif
 }
+HD DualD rsqrt_hd(DualD x) {
+  const double r = rsqrt_hd(x.v);
+  return DualD(r, -0.5 * r * r * r * x.d);
+}
 
 // dynamic viscosity at temperature ratio t = T/T_inf = gamma p/rho (free stream rho 1, p 1/gamma):
 // constant, or Sutherland's law mu_inf t^(3/2) (1 + s)/(t + s)
-HD double viscosity(const Phys& ph, double t) {
-  if (ph.suth == 0.0) return ph.mu;
+template <typename T>
+HD T viscosity(const Phys& ph, T t) {
+  if (ph.suth == 0.0) return T(ph.mu);
   return ph.mu * t * sqrt(t) * (1.0 + ph.suth) / (t + ph.suth);
 }
 
@@ -44,15 +56,29 @@ struct ReconArgs {
   DevErr* err;
 };
 
-HD void reconstruct_body(int64_t i, const ReconArgs& a) {
+// value of stencil input c of slot s as T: with T = DualD the one seeded input carries derivative 1
+template <typename T>
+struct Seed {
+  HD static T at(double v, bool) { return v; }
+};
+template <>
+struct Seed<DualD> {
+  HD static DualD at(double v, bool on) { return DualD(v, on ? 1.0 : 0.0); }
+};
+
+// reconstruction of cell i: 10 coefficients per variable.  Seeds of the
+// forward-mode linearisation: 20 s + c is component c of (W 5, grad W 15) of stencil slot s (slot 0
+// the cell, slot 1 + m its neighbour through local face m); seed < 0 for none
+template <typename T>
+HD void reconstruct_cell(int64_t i, const ReconArgs& a, int seed, T out[CGKS_RC]) {
   const int64_t nc = a.nc, nf = a.nf;
   const int nt = a.ctype[i] == 7 ? 5 : a.ctype[i];  // faces: pyramids (type 7) have 5
   const Phys& ph = a.ph;
-  double Q0[5];
+  T Q0[5];
 #pragma unroll
-  for (int q = 0; q < 5; ++q) Q0[q] = a.W[q * nc + i];
+  for (int q = 0; q < 5; ++q) Q0[q] = Seed<T>::at(a.W[q * nc + i], seed == q);
   // p^2 coefficients b[q][j] of X,Y,Z,X^2,Y^2,Z^2,XY,YZ,XZ; Green-Gauss and least-squares gradients
-  double b[5][9], gg[5][3], gl[5][3];
+  T b[5][9], gg[5][3], gl[5][3];
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
 #pragma unroll
@@ -62,21 +88,22 @@ HD void reconstruct_body(int64_t i, const ReconArgs& a) {
   }
   for (int m = 0; m < nt; ++m) {
     const int64_t f = a.cf[(int64_t)m * nc + i];
-    double Qn[5], Gn[15];
+    T Qn[5], Gn[15];
     if (a.fR[f] >= 0) {
       const int64_t nb = a.cside[(int64_t)m * nc + i] ? a.fL[f] : a.fR[f];
+      const int s0 = 20 * (m + 1);
 #pragma unroll
-      for (int q = 0; q < 5; ++q) Qn[q] = a.W[q * nc + nb];
+      for (int q = 0; q < 5; ++q) Qn[q] = Seed<T>::at(a.W[q * nc + nb], seed == s0 + q);
 #pragma unroll
-      for (int j = 0; j < 15; ++j) Gn[j] = a.G[j * nc + nb];
+      for (int j = 0; j < 15; ++j) Gn[j] = Seed<T>::at(a.G[j * nc + nb], seed == s0 + 5 + j);
     } else {
-      double G0[15];
+      T G0[15];
 #pragma unroll
-      for (int j = 0; j < 15; ++j) G0[j] = a.G[j * nc + i];
-      const double n[3] = {a.fnrm[f], a.fnrm[nf + f], a.fnrm[2 * nf + f]};
-      if (!bc_ghost<double>(a.ftag[f], n, Q0, G0, Qn, Gn, ph.gamma, ph.Winf)) set_err(a.err, CGKS_ENAN, (int)i, 1);
+      for (int j = 0; j < 15; ++j) G0[j] = Seed<T>::at(a.G[j * nc + i], seed == 5 + j);
+      const T n[3] = {a.fnrm[f], a.fnrm[nf + f], a.fnrm[2 * nf + f]};
+      if (!bc_ghost<T>(a.ftag[f], n, Q0, G0, Qn, Gn, T(ph.gamma), ph.Winf)) set_err(a.err, CGKS_ENAN, (int)i, 1);
     }
-    double dQ[5];
+    T dQ[5];
 #pragma unroll
     for (int q = 0; q < 5; ++q) dQ[q] = Qn[q] - Q0[q];
     // the difference column and the three gradient columns of this neighbour
@@ -105,75 +132,118 @@ HD void reconstruct_body(int64_t i, const ReconArgs& a) {
   for (int j = 0; j < 6; ++j) M2[j] = a.aux[(2 + j) * nc + i];
   const double al = a.alpha[i];
   const double g1 = 0.5, g2 = 0.5;
-  __align__(16) double out[CGKS_RC];
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
-    const double* bq = b[q];
-    const double a0 = Q0[q] - (bq[3] * M2[0] + bq[4] * M2[1] + bq[5] * M2[2] + bq[6] * M2[3] + bq[7] * M2[4] + bq[8] * M2[5]);
-    const double p1[3] = {al * gg[q][0], al * gg[q][1], al * gg[q][2]};
-    const double bGG = V23 * (p1[0] * p1[0] + p1[1] * p1[1] + p1[2] * p1[2]);
-    const double bLS = V23 * (gl[q][0] * gl[q][0] + gl[q][1] * gl[q][1] + gl[q][2] * gl[q][2]);
-    const double beta1 = fmin(bGG, bLS);
+    const T* bq = b[q];
+    const T a0 = Q0[q] - (bq[3] * M2[0] + bq[4] * M2[1] + bq[5] * M2[2] + bq[6] * M2[3] + bq[7] * M2[4] + bq[8] * M2[5]);
+    const T p1[3] = {al * gg[q][0], al * gg[q][1], al * gg[q][2]};
+    const T bGG = V23 * (p1[0] * p1[0] + p1[1] * p1[1] + p1[2] * p1[2]);
+    const T bLS = V23 * (gl[q][0] * gl[q][0] + gl[q][1] * gl[q][1] + gl[q][2] * gl[q][2]);
+    const T beta1 = fmin(bGG, bLS);
     // |Omega|^(2/3) sum_d (avg of (d_d p2)^2) + |Omega|^(4/3) sum_{|a|=2} (D^a p2)^2
-    const double v[3][3] = {{2.0 * bq[3], bq[6], bq[8]}, {bq[6], 2.0 * bq[4], bq[7]}, {bq[8], bq[7], 2.0 * bq[5]}};
-    double first = 0.0;
+    const T v[3][3] = {{2.0 * bq[3], bq[6], bq[8]}, {bq[6], 2.0 * bq[4], bq[7]}, {bq[8], bq[7], 2.0 * bq[5]}};
+    T first = 0.0;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      const double* x = v[d];
-      const double vMv = M2[0] * x[0] * x[0] + M2[1] * x[1] * x[1] + M2[2] * x[2] * x[2] +
-                         2.0 * (M2[3] * x[0] * x[1] + M2[4] * x[1] * x[2] + M2[5] * x[0] * x[2]);
+      const T* x = v[d];
+      const T vMv = M2[0] * x[0] * x[0] + M2[1] * x[1] * x[1] + M2[2] * x[2] * x[2] +
+                    2.0 * (M2[3] * x[0] * x[1] + M2[4] * x[1] * x[2] + M2[5] * x[0] * x[2]);
       first += bq[d] * bq[d] + vMv;
     }
-    const double second = 4.0 * (bq[3] * bq[3] + bq[4] * bq[4] + bq[5] * bq[5]) + bq[6] * bq[6] + bq[7] * bq[7] + bq[8] * bq[8];
-    const double beta2 = V23 * first + V43 * second;
-    const double rden = 1.0 / (Q0[q] * Q0[q] + beta1 + 1e-40);
-    const double bt1 = beta1 * rden, bt2 = beta2 * rden;
-    const double sig = fabs(bt2 - bt1);
+    const T second = 4.0 * (bq[3] * bq[3] + bq[4] * bq[4] + bq[5] * bq[5]) + bq[6] * bq[6] + bq[7] * bq[7] + bq[8] * bq[8];
+    const T beta2 = V23 * first + V43 * second;
+    const T rden = 1.0 / (Q0[q] * Q0[q] + beta1 + 1e-40);
+    const T bt1 = beta1 * rden, bt2 = beta2 * rden;
+    const T sig = fabs(bt2 - bt1);
     // w_m = g_m (1 + (sig/d_m)^2) with d_m = eps + beta~_m, normalised with one division:
     // w_1 : w_2 = g_1 (d_1^2 + sig^2) d_2^2 : g_2 (d_2^2 + sig^2) d_1^2
-    const double d1 = ph.weno_eps + bt1, d2 = ph.weno_eps + bt2;
-    const double s2 = sig * sig, d11 = d1 * d1, d22 = d2 * d2;
-    const double A1 = g1 * (d11 + s2) * d22, A2 = g2 * (d22 + s2) * d11;
-    const double inv = 1.0 / (A1 + A2);
-    const double w1 = A1 * inv, w2 = A2 * inv;
-    const double c2 = w2 * (1.0 / g2), c1 = w1 - w2 * (g1 / g2);
+    const T d1 = ph.weno_eps + bt1, d2 = ph.weno_eps + bt2;
+    const T s2 = sig * sig, d11 = d1 * d1, d22 = d2 * d2;
+    const T A1 = g1 * (d11 + s2) * d22, A2 = g2 * (d22 + s2) * d11;
+    const T inv = 1.0 / (A1 + A2);
+    const T w1 = A1 * inv, w2 = A2 * inv;
+    const T c2 = w2 * (1.0 / g2), c1 = w1 - w2 * (g1 / g2);
     out[10 * q + 0] = c2 * a0 + c1 * Q0[q];
 #pragma unroll
     for (int d = 0; d < 3; ++d) out[10 * q + 1 + d] = c2 * bq[d] + c1 * p1[d];
 #pragma unroll
     for (int j = 3; j < 9; ++j) out[10 * q + 1 + j] = c2 * bq[j];
   }
-  double2* dst = reinterpret_cast<double2*>(a.rc + (int64_t)CGKS_RC * i);
-#pragma unroll
-  for (int k = 0; k < CGKS_RC / 2; ++k) dst[k] = make_double2(out[2 * k], out[2 * k + 1]);
-  // local time step: CFL |Omega| / sum_p S_p (|U.n_p| + c + 2 nu S_p / |Omega|)
-  const double r = 1.0 / Q0[0];
-  const double u[3] = {Q0[1] * r, Q0[2] * r, Q0[3] * r};
-  const double p = (ph.gamma - 1.0) * (Q0[4] - 0.5 * Q0[0] * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
-  const double c = sqrt(ph.gamma * p * r);
+}
+
+// local time step of cell i from its average Q0: CFL |Omega| / sum_p S_p (|U.n_p| + c + 2 nu S_p / |Omega|)
+template <typename T>
+HD T time_step(int64_t i, const ReconArgs& a, const T Q0[5]) {
+  const int64_t nc = a.nc;
+  const int nt = a.ctype[i] == 7 ? 5 : a.ctype[i];
+  const Phys& ph = a.ph;
+  const T r = 1.0 / Q0[0];
+  const T u[3] = {Q0[1] * r, Q0[2] * r, Q0[3] * r};
+  const T p = (ph.gamma - 1.0) * (Q0[4] - 0.5 * Q0[0] * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
+  const T c = sqrt(ph.gamma * p * r);
   const double V = a.vol[i];
-  const double nu2 = ph.viscous ? 2.0 * viscosity(ph, ph.gamma * p * r) * r / V : 0.0;
-  double s = 0.0;
+  const T nu2 = ph.viscous ? 2.0 * viscosity<T>(ph, ph.gamma * p * r) * r / V : T(0.0);
+  T s = 0.0;
   for (int m = 0; m < nt; ++m) {
     const double S = a.dtw[(4 * m + 3) * nc + i];
-    const double un = fabs(u[0] * a.dtw[(4 * m) * nc + i] + u[1] * a.dtw[(4 * m + 1) * nc + i] +
-                           u[2] * a.dtw[(4 * m + 2) * nc + i]);
+    const T un = fabs(u[0] * a.dtw[(4 * m) * nc + i] + u[1] * a.dtw[(4 * m + 1) * nc + i] +
+                      u[2] * a.dtw[(4 * m + 2) * nc + i]);
     s += un + S * c + nu2 * S * S;
   }
-  a.dt[i] = ph.cfl_fine * V / s;
   if (!(Q0[0] > 0.0) || !(p > 0.0) || !isfinite(Q0[4])) set_err(a.err, CGKS_ENAN, (int)i, 2);
+  return ph.cfl_fine * V / s;
+}
+
+HD void reconstruct_body(int64_t i, const ReconArgs& a) {
+  {
+    __align__(16) double out[CGKS_RC];
+    reconstruct_cell<double>(i, a, -1, out);
+    double2* dst = reinterpret_cast<double2*>(a.rc + (int64_t)CGKS_RC * i);
+#pragma unroll
+    for (int k = 0; k < CGKS_RC / 2; ++k) dst[k] = make_double2(out[2 * k], out[2 * k + 1]);
+  }
+  double Q0[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) Q0[q] = a.W[q * a.nc + i];
+  a.dt[i] = time_step<double>(i, a, Q0);
+}
+
+// forward-mode linearisation of the reconstruction of cell i: Jr[(51 k + o) nc + i] = d out_o /
+// d in_k, outputs o = (the 50 coefficients, the time step), inputs k = 20 s + c as in
+// reconstruct_cell for the 1 + 6 stencil slots; columns of absent slots (boundary faces, fewer
+// faces) are zero
+HD void recon_jacobian_body(int64_t i, const ReconArgs& a, double* Jr) {
+  const int64_t nc = a.nc;
+  const int nt = a.ctype[i] == 7 ? 5 : a.ctype[i];
+  for (int k = 0; k < CGKS_RJ_IN; ++k) {
+    const int slot = k / 20;
+    bool live = slot == 0;
+    if (slot >= 1 && slot <= nt) live = a.fR[a.cf[(int64_t)(slot - 1) * nc + i]] >= 0;
+    DualD out[CGKS_RC];
+    if (live) reconstruct_cell<DualD>(i, a, k, out);
+    for (int o = 0; o < CGKS_RC; ++o) Jr[(int64_t)(CGKS_RJ_OUT * k + o) * nc + i] = live ? out[o].d : 0.0;
+    double ddt = 0.0;
+    if (k < 5) {
+      DualD Q0[5];
+      for (int q = 0; q < 5; ++q) Q0[q] = DualD(a.W[q * nc + i], q == k ? 1.0 : 0.0);
+      ddt = time_step<DualD>(i, a, Q0).d;
+    }
+    Jr[(int64_t)(CGKS_RJ_OUT * k + CGKS_RC) * nc + i] = ddt;
+  }
 }
 
 // ---- gas-kinetic point flux -------------------------------------------------------------------
 
 // a Maxwellian in the face frame with the reciprocals the moments and slopes need
+template <typename T>
 struct Maxw {
-  double rho, U, V, W;  // density, velocity (normal, tangential 1, tangential 2)
-  double r, p, h;       // 1/rho, pressure, h = p/rho = 1/(2 lambda)
-  double l2, q2;        // 2 lambda = 1/h, |U|^2 + (K+3) h
+  T rho, U, V, W;  // density, velocity (normal, tangential 1, tangential 2)
+  T r, p, h;       // 1/rho, pressure, h = p/rho = 1/(2 lambda)
+  T l2, q2;        // 2 lambda = 1/h, |U|^2 + (K+3) h
 };
 
-HD bool make_maxw(const double w[5], double gm1, double K, Maxw& g) {
+template <typename T>
+HD bool make_maxw(const T w[5], T gm1, T K, Maxw<T>& g) {
   g.rho = w[0];
   g.r = 1.0 / w[0];
   g.U = w[1] * g.r;
@@ -188,20 +258,22 @@ HD bool make_maxw(const double w[5], double gm1, double K, Maxw& g) {
 
 // <u^0>, <u^1> over u > 0 (side +1) or u < 0 (side -1), normalised by rho:
 // 1/2 erfc(-s sqrt(lambda) U) and U <u^0> + s exp(-lambda U^2) / (2 sqrt(pi lambda))
-HD void half_seeds(const Maxw& g, double side, double& m0, double& m1) {
-  const double lam = 0.5 * g.l2;
-  const double isl = rsqrt_hd(lam);
-  const double sl = lam * isl;
+template <typename T>
+HD void half_seeds(const Maxw<T>& g, T side, T& m0, T& m1) {
+  const T lam = 0.5 * g.l2;
+  const T isl = rsqrt_hd(lam);
+  const T sl = lam * isl;
   m0 = 0.5 * erfc(-side * sl * g.U);
   m1 = g.U * m0 + side * (0.5 * 0.56418958354775628695) * exp(-lam * g.U * g.U) * isl;
 }
 
 // micro-slope s with <s psi> = dW under the full Maxwellian g (closed form of the 5x5 system);
 // ck = 4 lambda^2 / (K + 3)
-HD void slope_solve(const Maxw& g, double ck, const double dW[5], double s[5]) {
-  const double d0 = dW[0] * g.r, d1 = dW[1] * g.r, d2 = dW[2] * g.r, d3 = dW[3] * g.r, d4 = dW[4] * g.r;
-  const double R4 = 2.0 * d4 - g.q2 * d0;
-  const double R1 = d1 - g.U * d0, R2 = d2 - g.V * d0, R3 = d3 - g.W * d0;
+template <typename T>
+HD void slope_solve(const Maxw<T>& g, T ck, const T dW[5], T s[5]) {
+  const T d0 = dW[0] * g.r, d1 = dW[1] * g.r, d2 = dW[2] * g.r, d3 = dW[3] * g.r, d4 = dW[4] * g.r;
+  const T R4 = 2.0 * d4 - g.q2 * d0;
+  const T R1 = d1 - g.U * d0, R2 = d2 - g.V * d0, R3 = d3 - g.W * d0;
   s[4] = ck * (R4 - 2.0 * (g.U * R1 + g.V * R2 + g.W * R3));
   s[1] = g.l2 * R1 - g.U * s[4];
   s[2] = g.l2 * R2 - g.V * s[4];
@@ -211,12 +283,13 @@ HD void slope_solve(const Maxw& g, double ck, const double dW[5], double s[5]) {
 
 // directional derivative of the Euler flux through the k-th axis of the face frame along dW:
 // equals <u_k (a . psi) psi> under the full Maxwellian when <a psi> = dW
-HD void euler_jvp(const double w[5], const Maxw& g, double gm1, int k, const double dW[5], double out[5]) {
-  const double u[3] = {g.U, g.V, g.W};
-  const double du[3] = {(dW[1] - u[0] * dW[0]) * g.r, (dW[2] - u[1] * dW[0]) * g.r, (dW[3] - u[2] * dW[0]) * g.r};
-  const double dp = gm1 * (dW[4] - (u[0] * dW[1] + u[1] * dW[2] + u[2] * dW[3]) +
+template <typename T>
+HD void euler_jvp(const T w[5], const Maxw<T>& g, T gm1, int k, const T dW[5], T out[5]) {
+  const T u[3] = {g.U, g.V, g.W};
+  const T du[3] = {(dW[1] - u[0] * dW[0]) * g.r, (dW[2] - u[1] * dW[0]) * g.r, (dW[3] - u[2] * dW[0]) * g.r};
+  const T dp = gm1 * (dW[4] - (u[0] * dW[1] + u[1] * dW[2] + u[2] * dW[3]) +
                            0.5 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) * dW[0]);
-  const double mk = w[1 + k], dmk = dW[1 + k];
+  const T mk = w[1 + k], dmk = dW[1 + k];
   out[0] = dmk;
 #pragma unroll
   for (int j = 0; j < 3; ++j) out[1 + j] = dmk * u[j] + mk * du[j];
@@ -249,11 +322,12 @@ HD void eval_value(const double* rcp, const double X[3], double Wv[5]) {
 }
 
 // directional derivatives along (n, t1, t2) of the frame-rotated conservative variables
-HD void rotate_gradient(const double Gq[15], const double* e[3], double D[3][5]) {
+template <typename T>
+HD void rotate_gradient(const T Gq[15], const T* e[3], T D[3][5]) {
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const double* dir = e[k];
-    double gs[5];
+    const T* dir = e[k];
+    T gs[5];
 #pragma unroll
     for (int q = 0; q < 5; ++q) gs[q] = Gq[3 * q] * dir[0] + Gq[3 * q + 1] * dir[1] + Gq[3 * q + 2] * dir[2];
     D[k][0] = gs[0];
@@ -268,22 +342,24 @@ HD void rotate_gradient(const double Gq[15], const double* e[3], double D[3][5])
 // psi' = (1, u, c, d, (u^2 + c^2 + d^2 + xi^2)/2) and T adds V, W, (V^2 + W^2)/2 terms.  Odd moments of
 // c and d vanish, so the matrices <u^k psi' psi'^T>, <u^k c psi' psi'^T>, <u^k d psi' psi'^T> are sparse;
 // a slope s becomes s' = T^T s and a moment vector o' becomes T o'.
+template <typename T>
 struct MomP {
-  double M[7];            // rho <u^k>, k = 0..6 (half or full space)
-  double h, sig, tau4;    // h = p/rho, sig = h + <xi^2>/2, tau4 = 2 h^2 + h <xi^2> + <xi^4>/4
-  double hs;              // h (2 h + <xi^2>/2)
-  double V, W, E;         // tangential velocity and (V^2 + W^2)/2
+  T M[7];            // rho <u^k>, k = 0..6 (half or full space)
+  T h, sig, tau4;    // h = p/rho, sig = h + <xi^2>/2, tau4 = 2 h^2 + h <xi^2> + <xi^4>/4
+  T hs;              // h (2 h + <xi^2>/2)
+  T V, W, E;         // tangential velocity and (V^2 + W^2)/2
 };
 
-HD void make_momp(const Maxw& g, double m0, double m1, double K, MomP& P) {
-  double m[7];
+template <typename T>
+HD void make_momp(const Maxw<T>& g, T m0, T m1, T K, MomP<T>& P) {
+  T m[7];
   m[0] = m0;
   m[1] = m1;
 #pragma unroll
   for (int n = 0; n + 2 < 7; ++n) m[n + 2] = g.U * m[n + 1] + (n + 1) * g.h * m[n];
 #pragma unroll
   for (int k = 0; k < 7; ++k) P.M[k] = g.rho * m[k];
-  const double h = g.h, x2 = K * h, x4 = K * (K + 2.0) * h * h;
+  const T h = g.h, x2 = K * h, x4 = K * (K + 2.0) * h * h;
   P.h = h;
   P.sig = h + 0.5 * x2;
   P.tau4 = 2.0 * h * h + h * x2 + 0.25 * x4;
@@ -294,7 +370,8 @@ HD void make_momp(const Maxw& g, double m0, double m1, double K, MomP& P) {
 }
 
 // s' = T^T s
-HD void to_primed(const MomP& P, const double s[5], double sp[5]) {
+template <typename T>
+HD void to_primed(const MomP<T>& P, const T s[5], T sp[5]) {
   sp[0] = s[0] + P.V * s[2] + P.W * s[3] + P.E * s[4];
   sp[1] = s[1];
   sp[2] = s[2] + P.V * s[4];
@@ -303,7 +380,8 @@ HD void to_primed(const MomP& P, const double s[5], double sp[5]) {
 }
 
 // out += c T o'
-HD void add_from_primed(const MomP& P, const double o[5], double c, double out[5]) {
+template <typename T>
+HD void add_from_primed(const MomP<T>& P, const T o[5], T c, T out[5]) {
   out[0] += c * o[0];
   out[1] += c * o[1];
   out[2] += c * (P.V * o[0] + o[2]);
@@ -312,13 +390,13 @@ HD void add_from_primed(const MomP& P, const double o[5], double c, double out[5
 }
 
 // o' = <u^k (s' . psi') psi'>
-template <int k>
-HD void papp(const MomP& P, const double s[5], double o[5]) {
-  const double* M = P.M;
-  const double Pk = 0.5 * M[k + 2] + P.sig * M[k];
-  const double Qk = 0.5 * M[k + 3] + P.sig * M[k + 1];
-  const double Rk = 0.25 * M[k + 4] + P.sig * M[k + 2] + P.tau4 * M[k];
-  const double hM = P.h * M[k];
+template <typename T, int k>
+HD void papp(const MomP<T>& P, const T s[5], T o[5]) {
+  const T* M = P.M;
+  const T Pk = 0.5 * M[k + 2] + P.sig * M[k];
+  const T Qk = 0.5 * M[k + 3] + P.sig * M[k + 1];
+  const T Rk = 0.25 * M[k + 4] + P.sig * M[k + 2] + P.tau4 * M[k];
+  const T hM = P.h * M[k];
   o[0] = M[k] * s[0] + M[k + 1] * s[1] + Pk * s[4];
   o[1] = M[k + 1] * s[0] + M[k + 2] * s[1] + Qk * s[4];
   o[2] = hM * s[2];
@@ -327,11 +405,11 @@ HD void papp(const MomP& P, const double s[5], double o[5]) {
 }
 
 // o' += <u^k c (s' . psi') psi'> (J = 2) or <u^k d (s' . psi') psi'> (J = 3)
-template <int k, int J>
-HD void papp_t_add(const MomP& P, const double s[5], double o[5]) {
-  const double* M = P.M;
-  const double hM0 = P.h * M[k], hM1 = P.h * M[k + 1];
-  const double S4 = 0.5 * P.h * M[k + 2] + P.hs * M[k];
+template <typename T, int k, int J>
+HD void papp_t_add(const MomP<T>& P, const T s[5], T o[5]) {
+  const T* M = P.M;
+  const T hM0 = P.h * M[k], hM1 = P.h * M[k + 1];
+  const T S4 = 0.5 * P.h * M[k + 2] + P.hs * M[k];
   o[0] += hM0 * s[J];
   o[1] += hM1 * s[J];
   o[J] += hM0 * s[0] + hM1 * s[1] + S4 * s[4];
@@ -340,73 +418,74 @@ HD void papp_t_add(const MomP& P, const double s[5], double o[5]) {
 
 // o' = <u^k (a . u) psi'> with the three slopes in primed form: u a_n + v a_t1 + w a_t2,
 // v = V + c, w = W + d
-template <int k>
-HD void papp_au(const MomP& P, const double an[5], const double a1[5], const double a2[5], double o[5]) {
-  double comb[5], t[5];
+template <typename T, int k>
+HD void papp_au(const MomP<T>& P, const T an[5], const T a1[5], const T a2[5], T o[5]) {
+  T comb[5], t[5];
 #pragma unroll
   for (int q = 0; q < 5; ++q) comb[q] = P.V * a1[q] + P.W * a2[q];
-  papp<k + 1>(P, an, o);
-  papp<k>(P, comb, t);
+  papp<T, k + 1>(P, an, o);
+  papp<T, k>(P, comb, t);
 #pragma unroll
   for (int q = 0; q < 5; ++q) o[q] += t[q];
-  papp_t_add<k, 2>(P, a1, o);
-  papp_t_add<k, 3>(P, a2, o);
+  papp_t_add<T, k, 2>(P, a1, o);
+  papp_t_add<T, k, 3>(P, a2, o);
 }
 
 // one side of the interface: micro-slopes of the initial distribution, its contribution to the
 // equilibrium slopes, the time-integrated flux, the state at dt and the time-integrated state
-HD void side_terms(const double D[3][5], const double w[5], const Maxw& g, double m0, double m1, double K, double ck,
-                   double gm1, double tau, double q4, double q5, double edt, double dtf, double dWc[3][5],
-                   double Facc[5], double Wacc[5], double Iacc[5]) {
-  MomP P;
-  make_momp(g, m0, m1, K, P);
-  double a[3][5];
+template <typename T>
+HD void side_terms(const T D[3][5], const T w[5], const Maxw<T>& g, T m0, T m1, T K, T ck,
+                   T gm1, T tau, T q4, T q5, T edt, T dtf, T dWc[3][5],
+                   T Facc[5], T Wacc[5], T Iacc[5]) {
+  MomP<T> P;
+  make_momp<T>(g, m0, m1, K, P);
+  T a[3][5];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    double s[5];
-    slope_solve(g, ck, D[k], s);
-    to_primed(P, s, a[k]);
+    T s[5];
+    slope_solve<T>(g, ck, D[k], s);
+    to_primed<T>(P, s, a[k]);
   }
   // time slope A from <A + a.u> = 0 under the full Maxwellian: <(a.u) psi> = sum_k J_k dW_k
-  double Ap[5];
+  T Ap[5];
   {
-    double t0[5], t1[5], t2[5], au[5], A[5];
-    euler_jvp(w, g, gm1, 0, D[0], t0);
-    euler_jvp(w, g, gm1, 1, D[1], t1);
-    euler_jvp(w, g, gm1, 2, D[2], t2);
+    T t0[5], t1[5], t2[5], au[5], A[5];
+    euler_jvp<T>(w, g, gm1, 0, D[0], t0);
+    euler_jvp<T>(w, g, gm1, 1, D[1], t1);
+    euler_jvp<T>(w, g, gm1, 2, D[2], t2);
 #pragma unroll
     for (int q = 0; q < 5; ++q) au[q] = -(t0[q] + t1[q] + t2[q]);
-    slope_solve(g, ck, au, A);
-    to_primed(P, A, Ap);
+    slope_solve<T>(g, ck, au, A);
+    to_primed<T>(P, A, Ap);
   }
   // half-space moments: equilibrium-slope contributions <a_k psi>
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    double t[5];
-    papp<0>(P, a[k], t);
-    add_from_primed(P, t, 1.0, dWc[k]);
+    T t[5];
+    papp<T, 0>(P, a[k], t);
+    add_from_primed<T>(P, t, 1.0, dWc[k]);
   }
   // <(a.u) psi>, <u (a.u) psi>, <A psi>, <u A psi>, <psi>, <u psi>
-  double Va[5], Fa[5], VA[5], FA[5];
-  papp_au<0>(P, a[0], a[1], a[2], Va);
-  papp_au<1>(P, a[0], a[1], a[2], Fa);
-  papp<0>(P, Ap, VA);
-  papp<1>(P, Ap, FA);
-  const double* M = P.M;
-  const double V0[5] = {M[0], M[1], 0.0, 0.0, 0.5 * M[2] + P.sig * M[0]};
-  const double F0[5] = {M[1], M[2], 0.0, 0.0, 0.5 * M[3] + P.sig * M[1]};
-  const double tq4 = tau * q4;
-  const double etd = edt * (tau + dtf), etau = edt * tau;
-  double f[5], s[5], i[5];
+  T Va[5], Fa[5], VA[5], FA[5];
+  papp_au<T, 0>(P, a[0], a[1], a[2], Va);
+  papp_au<T, 1>(P, a[0], a[1], a[2], Fa);
+  papp<T, 0>(P, Ap, VA);
+  papp<T, 1>(P, Ap, FA);
+  const T* M = P.M;
+  const T V0[5] = {M[0], M[1], 0.0, 0.0, 0.5 * M[2] + P.sig * M[0]};
+  const T F0[5] = {M[1], M[2], 0.0, 0.0, 0.5 * M[3] + P.sig * M[1]};
+  const T tq4 = tau * q4;
+  const T etd = edt * (tau + dtf), etau = edt * tau;
+  T f[5], s[5], i[5];
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
     f[q] = q4 * F0[q] - q5 * Fa[q] - tq4 * FA[q];
     s[q] = edt * V0[q] - etd * Va[q] - etau * VA[q];
     i[q] = q4 * V0[q] - q5 * Va[q] - tq4 * VA[q];
   }
-  add_from_primed(P, f, 1.0, Facc);
-  add_from_primed(P, s, 1.0, Wacc);
-  add_from_primed(P, i, 1.0, Iacc);
+  add_from_primed<T>(P, f, 1.0, Facc);
+  add_from_primed<T>(P, s, 1.0, Wacc);
+  add_from_primed<T>(P, i, 1.0, Iacc);
 }
 
 struct PointArgs {
@@ -418,117 +497,143 @@ struct PointArgs {
   DevErr* err;
 };
 
-HD void gks_point_body(int64_t g, const PointArgs& a) {
-  const Phys& ph = a.ph;
+// inputs of one Gauss point: unit normal n, 1/|weight x area|, face, cells, the left and right
+// states and gradients at the point (global frame) and the face's time step
+struct PointIn {
+  double n[3], iw;
+  int64_t f, L, R;
+  double WL[5], GL[15], WR[5], GR[15], dtf;
+};
+
+HD void point_inputs(int64_t g, const PointArgs& a, PointIn& p) {
   const int64_t ngp = a.ngp, nf = a.nf, nc = a.nc;
   const int64_t f = a.gp_face[g];
   const int64_t L = a.fL[f], R = a.fR[f];
+  p.f = f;
+  p.L = L;
+  p.R = R;
   const double x[3] = {a.gp_x[g], a.gp_x[ngp + g], a.gp_x[2 * ngp + g]};
   const double Av[3] = {a.gp_A[g], a.gp_A[ngp + g], a.gp_A[2 * ngp + g]};
-  const double iw = rsqrt_hd(Av[0] * Av[0] + Av[1] * Av[1] + Av[2] * Av[2]);
-  const double n[3] = {Av[0] * iw, Av[1] * iw, Av[2] * iw};
-  double t1[3], t2[3];
-  face_frame(n, t1, t2);
-  const double* e[3] = {n, t1, t2};
-  const double K = ph.K, gm1 = ph.gamma - 1.0, iK3 = 1.0 / (K + 3.0);
-  const bool bnd = R < 0;
-  // left and right states and gradients at the point (global frame)
+  p.iw = rsqrt_hd(Av[0] * Av[0] + Av[1] * Av[1] + Av[2] * Av[2]);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) p.n[d] = Av[d] * p.iw;
   const double* rcL = a.rc + (int64_t)CGKS_RC * L;
   const double XL[3] = {x[0] - a.ctr[L], x[1] - a.ctr[nc + L], x[2] - a.ctr[2 * nc + L]};
-  double WLg[5], WRg[5], GLg[15], GRg[15], dtf;
-  eval_value(rcL, XL, WLg);
-  eval_gradient(rcL, XL, GLg);
-  if (!bnd) {
+  eval_value(rcL, XL, p.WL);
+  eval_gradient(rcL, XL, p.GL);
+  if (R >= 0) {
     const double* rcR = a.rc + (int64_t)CGKS_RC * R;
     double XR[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) XR[d] = x[d] - a.fshift[d * nf + f] - a.ctr[d * nc + R];
-    eval_value(rcR, XR, WRg);
-    eval_gradient(rcR, XR, GRg);
-    dtf = fmin(a.dt[L], a.dt[R]);
+    eval_value(rcR, XR, p.WR);
+    eval_gradient(rcR, XR, p.GR);
+    p.dtf = fmin(a.dt[L], a.dt[R]);
   } else {
-    if (!bc_ghost<double>(a.ftag[f], n, WLg, GLg, WRg, GRg, ph.gamma, ph.Winf)) set_err(a.err, CGKS_ENAN, (int)f, 3);
-    dtf = a.dt[L];
+    p.dtf = a.dt[L];
   }
-  double wl[5], wr[5];
-  rotate_in(WLg, n, t1, t2, wl);
-  rotate_in(WRg, n, t1, t2, wr);
-  Maxw gl, gr;
-  const bool okl = make_maxw(wl, gm1, K, gl), okr = make_maxw(wr, gm1, K, gr);
-  if (!(okl && okr)) set_err(a.err, CGKS_ENAN, (int)f, 4);
+}
+
+// the gas-kinetic flux of one Gauss point (flux x weight / dt and interface state x area, both in
+// the global frame) and its compression factor, from the point's left and right states and
+// gradients; on a boundary face (bnd) the right side is the ghost of the left
+template <typename T>
+HD void point_flux(const double nd[3], double iw, bool bnd, int tag, const T WLg[5], const T GLg[15], const T WRi[5],
+                   const T GRi[15], T dtf, const Phys& ph, T Fg[5], T Wg[5], T& alpha, DevErr* err, int64_t f) {
+  T n[3], t1[3], t2[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) n[d] = nd[d];
+  face_frame<T>(n, t1, t2);
+  const T* e[3] = {n, t1, t2};
+  const T K = ph.K, gm1 = ph.gamma - 1.0, iK3 = 1.0 / (ph.K + 3.0);
+  T WRg[5], GRg[15];
+  if (!bnd) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) WRg[q] = WRi[q];
+#pragma unroll
+    for (int j = 0; j < 15; ++j) GRg[j] = GRi[j];
+  } else if (!bc_ghost<T>(tag, n, WLg, GLg, WRg, GRg, T(ph.gamma), ph.Winf)) {
+    set_err(err, CGKS_ENAN, (int)f, 3);
+  }
+  T wl[5], wr[5];
+  rotate_in<T>(WLg, n, t1, t2, wl);
+  rotate_in<T>(WRg, n, t1, t2, wr);
+  Maxw<T> gl, gr;
+  const bool okl = make_maxw<T>(wl, gm1, K, gl), okr = make_maxw<T>(wr, gm1, K, gr);
+  if (!(okl && okr)) set_err(err, CGKS_ENAN, (int)f, 4);
   // half-space seeds of both sides, and the interface equilibrium
   // W^c = int_{u>0} psi g^l + int_{u<0} psi g^r (Eq. compatibility2)
-  double ml0, ml1, mr0, mr1;
-  half_seeds(gl, 1.0, ml0, ml1);
-  half_seeds(gr, -1.0, mr0, mr1);
-  double wc[5];
+  T ml0, ml1, mr0, mr1;
+  half_seeds<T>(gl, 1.0, ml0, ml1);
+  half_seeds<T>(gr, -1.0, mr0, mr1);
+  T wc[5];
   {
-    const double ml2 = gl.U * ml1 + gl.h * ml0, mr2 = gr.U * mr1 + gr.h * mr0;
-    const double ql = gl.V * gl.V + gl.W * gl.W + (K + 2.0) * gl.h;
-    const double qr = gr.V * gr.V + gr.W * gr.W + (K + 2.0) * gr.h;
+    const T ml2 = gl.U * ml1 + gl.h * ml0, mr2 = gr.U * mr1 + gr.h * mr0;
+    const T ql = gl.V * gl.V + gl.W * gl.W + (ph.K + 2.0) * gl.h;
+    const T qr = gr.V * gr.V + gr.W * gr.W + (ph.K + 2.0) * gr.h;
     wc[0] = gl.rho * ml0 + gr.rho * mr0;
     wc[1] = gl.rho * ml1 + gr.rho * mr1;
     wc[2] = gl.rho * gl.V * ml0 + gr.rho * gr.V * mr0;
     wc[3] = gl.rho * gl.W * ml0 + gr.rho * gr.W * mr0;
     wc[4] = 0.5 * (gl.rho * (ml2 + ml0 * ql) + gr.rho * (mr2 + mr0 * qr));
   }
-  Maxw gc;
-  if (!make_maxw(wc, gm1, K, gc)) set_err(a.err, CGKS_ENAN, (int)f, 5);
+  Maxw<T> gc;
+  if (!make_maxw<T>(wc, gm1, K, gc)) set_err(err, CGKS_ENAN, (int)f, 5);
   // collision times (Sec. 2.3)
-  const double jump = fabs((gl.p - gr.p) / (gl.p + gr.p));
-  double tau, tn;
+  const T jump = fabs((gl.p - gr.p) / (gl.p + gr.p));
+  T tau, tn;
   if (ph.viscous) {
-    tau = viscosity(ph, ph.gamma * gc.h) * (gc.r * gc.l2);  // mu(T^c) / p^c, p^c/rho^c = 1/(2 lambda^c)
+    tau = viscosity<T>(ph, ph.gamma * gc.h) * (gc.r * gc.l2);  // mu(T^c) / p^c, p^c/rho^c = 1/(2 lambda^c)
     tn = tau + ph.c_press * jump * dtf;
   } else {
     tn = (ph.eps_inviscid + ph.c_press * jump) * dtf;
     tau = tn;
   }
   // exact integrals over [0, dt] of the time coefficients of Eq. 2nd-flux
-  const double edt = exp(-dtf / tn), om = 1.0 - edt;
-  const double q1 = dtf - tn * om;
-  const double q2 = (tn * tn + tau * tn) * om - tn * dtf * edt - tau * dtf;
-  const double q3 = 0.5 * dtf * dtf - tau * dtf + tau * tn * om;
-  const double q4 = tn * om;
-  const double q5 = (tau * tn + tn * tn) * om - tn * dtf * edt;
+  const T edt = exp(-dtf / tn), om = 1.0 - edt;
+  const T q1 = dtf - tn * om;
+  const T q2 = (tn * tn + tau * tn) * om - tn * dtf * edt - tau * dtf;
+  const T q3 = 0.5 * dtf * dtf - tau * dtf + tau * tn * om;
+  const T q4 = tn * om;
+  const T q5 = (tau * tn + tn * tn) * om - tn * dtf * edt;
   // compression factor of this Gauss point (interior faces only), 1/p = l2 / rho
-  double alpha = 1.0;
+  alpha = 1.0;
   if (!bnd && ph.cf) {
-    const double icl = rsqrt_hd(ph.gamma * gl.h), icr = rsqrt_hd(ph.gamma * gr.h);
-    const double dp = fabs(gl.p - gr.p);
-    const double dn = gl.U * icl - gr.U * icr, d1 = gl.V * icl - gr.V * icr, d2 = gl.W * icl - gr.W * icr;
-    const double A = dp * (gl.r * gl.l2 + gr.r * gr.l2) + dn * dn + (d1 * d1 + d2 * d2);
+    const T icl = rsqrt_hd(ph.gamma * gl.h), icr = rsqrt_hd(ph.gamma * gr.h);
+    const T dp = fabs(gl.p - gr.p);
+    const T dn = gl.U * icl - gr.U * icr, d1 = gl.V * icl - gr.V * icr, d2 = gl.W * icl - gr.W * icr;
+    const T A = dp * (gl.r * gl.l2 + gr.r * gr.l2) + dn * dn + (d1 * d1 + d2 * d2);
     alpha = 1.0 / (1.0 + A * A);
   }
-  double dWc[3][5], Facc[5], Wacc[5], Iacc[5];
+  T dWc[3][5], Facc[5], Wacc[5], Iacc[5];
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
     dWc[0][q] = dWc[1][q] = dWc[2][q] = 0.0;
     Facc[q] = Wacc[q] = Iacc[q] = 0.0;
   }
   {
-    double D[3][5];
-    rotate_gradient(GLg, e, D);
-    side_terms(D, wl, gl, ml0, ml1, K, gl.l2 * gl.l2 * iK3, gm1, tau, q4, q5, edt, dtf, dWc, Facc, Wacc, Iacc);
-    rotate_gradient(GRg, e, D);
-    side_terms(D, wr, gr, mr0, mr1, K, gr.l2 * gr.l2 * iK3, gm1, tau, q4, q5, edt, dtf, dWc, Facc, Wacc, Iacc);
+    T D[3][5];
+    rotate_gradient<T>(GLg, e, D);
+    side_terms<T>(D, wl, gl, ml0, ml1, K, gl.l2 * gl.l2 * iK3, gm1, tau, q4, q5, edt, dtf, dWc, Facc, Wacc, Iacc);
+    rotate_gradient<T>(GRg, e, D);
+    side_terms<T>(D, wr, gr, mr0, mr1, K, gr.l2 * gr.l2 * iK3, gm1, tau, q4, q5, edt, dtf, dWc, Facc, Wacc, Iacc);
   }
   // equilibrium part: slopes a^c from the kinetic-weighted interface gradients; A^c from
   // <A + a.u> = 0; full-space moments through the Euler-flux Jacobians
-  const double ckc = gc.l2 * gc.l2 * iK3;
-  double ac[3][5];
+  const T ckc = gc.l2 * gc.l2 * iK3;
+  T ac[3][5];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) slope_solve(gc, ckc, dWc[k], ac[k]);
-  double cu[5];  // <(a^c . u) psi>_c = sum_k J_k dW^c_k
+  for (int k = 0; k < 3; ++k) slope_solve<T>(gc, ckc, dWc[k], ac[k]);
+  T cu[5];  // <(a^c . u) psi>_c = sum_k J_k dW^c_k
   {
-    double t0[5], t1[5], t2[5];
-    euler_jvp(wc, gc, gm1, 0, dWc[0], t0);
-    euler_jvp(wc, gc, gm1, 1, dWc[1], t1);
-    euler_jvp(wc, gc, gm1, 2, dWc[2], t2);
+    T u0[5], u1[5], u2[5];
+    euler_jvp<T>(wc, gc, gm1, 0, dWc[0], u0);
+    euler_jvp<T>(wc, gc, gm1, 1, dWc[1], u1);
+    euler_jvp<T>(wc, gc, gm1, 2, dWc[2], u2);
 #pragma unroll
-    for (int q = 0; q < 5; ++q) cu[q] = t0[q] + t1[q] + t2[q];
+    for (int q = 0; q < 5; ++q) cu[q] = u0[q] + u1[q] + u2[q];
   }
-  double Fc0[5], FcA[5], Fca[5];
+  T Fc0[5], FcA[5], Fca[5];
   {
     // <u psi>_c is the Euler flux of W^c; <u A^c psi>_c = J_n <A^c psi>_c = -J_n <(a^c . u) psi>_c
     Fc0[0] = wc[1];
@@ -536,20 +641,20 @@ HD void gks_point_body(int64_t g, const PointArgs& a) {
     Fc0[2] = wc[2] * gc.U;
     Fc0[3] = wc[3] * gc.U;
     Fc0[4] = (wc[4] + gc.p) * gc.U;
-    euler_jvp(wc, gc, gm1, 0, cu, FcA);
+    euler_jvp<T>(wc, gc, gm1, 0, cu, FcA);
 #pragma unroll
     for (int q = 0; q < 5; ++q) FcA[q] = -FcA[q];
     // <u (a^c . u) psi>_c in the frame moving with the tangential velocity
-    MomP P;
-    make_momp(gc, 1.0, gc.U, K, P);
-    double a0[5], a1[5], a2[5], o[5];
-    to_primed(P, ac[0], a0);
-    to_primed(P, ac[1], a1);
-    to_primed(P, ac[2], a2);
-    papp_au<1>(P, a0, a1, a2, o);
+    MomP<T> P;
+    make_momp<T>(gc, 1.0, gc.U, K, P);
+    T a0[5], a1[5], a2[5], o[5];
+    to_primed<T>(P, ac[0], a0);
+    to_primed<T>(P, ac[1], a1);
+    to_primed<T>(P, ac[2], a2);
+    papp_au<T, 1>(P, a0, a1, a2, o);
 #pragma unroll
     for (int q = 0; q < 5; ++q) Fca[q] = 0.0;
-    add_from_primed(P, o, 1.0, Fca);
+    add_from_primed<T>(P, o, 1.0, Fca);
   }
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
@@ -559,24 +664,71 @@ HD void gks_point_body(int64_t g, const PointArgs& a) {
   }
   if (ph.viscous && ph.prandtl != 1.0) {
     // heat flux about U^c of the time-integrated distribution, scaled by (1/Pr - 1)
-    const double Ub[3] = {gc.U, gc.V, gc.W};
-    const double U2 = Ub[0] * Ub[0] + Ub[1] * Ub[1] + Ub[2] * Ub[2];
-    const double qn = Facc[4] - (Ub[0] * Facc[1] + Ub[1] * Facc[2] + Ub[2] * Facc[3]) + 0.5 * U2 * Facc[0] -
-                      Ub[0] * (Iacc[4] - (Ub[0] * Iacc[1] + Ub[1] * Iacc[2] + Ub[2] * Iacc[3]) + 0.5 * U2 * Iacc[0]);
+    const T Ub[3] = {gc.U, gc.V, gc.W};
+    const T U2 = Ub[0] * Ub[0] + Ub[1] * Ub[1] + Ub[2] * Ub[2];
+    const T qn = Facc[4] - (Ub[0] * Facc[1] + Ub[1] * Facc[2] + Ub[2] * Facc[3]) + 0.5 * U2 * Facc[0] -
+                 Ub[0] * (Iacc[4] - (Ub[0] * Iacc[1] + Ub[1] * Iacc[2] + Ub[2] * Iacc[3]) + 0.5 * U2 * Iacc[0]);
     Facc[4] += (1.0 / ph.prandtl - 1.0) * qn;
   }
-  const double sdt = 1.0 / (iw * dtf);  // weight / dt
+  const T sdt = 1.0 / (iw * dtf);  // weight / dt
 #pragma unroll
   for (int q = 0; q < 5; ++q) Facc[q] *= sdt;
-  double Fg[5], Wg[5];
-  rotate_out(Facc, n, t1, t2, Fg);
-  rotate_out(Wacc, n, t1, t2, Wg);
+  rotate_out<T>(Facc, n, t1, t2, Fg);
+  rotate_out<T>(Wacc, n, t1, t2, Wg);
+}
+
+HD void gks_point_body(int64_t g, const PointArgs& a) {
+  PointIn p;
+  point_inputs(g, a, p);
+  double Fg[5], Wg[5], alpha;
+  point_flux<double>(p.n, p.iw, p.R < 0, a.ftag[p.f], p.WL, p.GL, p.WR, p.GR, p.dtf, a.ph, Fg, Wg, alpha, a.err, p.f);
+  const int64_t ngp = a.ngp;
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
     a.gpF[q * ngp + g] = Fg[q];
     a.gpW[q * ngp + g] = Wg[q];
   }
   a.gpa[g] = alpha;
+}
+
+// forward-mode linearisation of one Gauss point: Jp[(10 k + o) ngp + g] = d out_o / d in_k with
+// inputs k = (W_L 5, grad W_L 15, W_R 5, grad W_R 15, dt_f) at the point and outputs o = (flux 5,
+// interface state 5) as gks_point_body stores them; the right-side columns of a boundary point
+// are zero (its ghost is a function of the left side)
+HD void point_jacobian_body(int64_t g, const PointArgs& a, double* Jp) {
+  PointIn p;
+  point_inputs(g, a, p);
+  const bool bnd = p.R < 0;
+  const int tag = a.ftag[p.f];
+  const int64_t ngp = a.ngp;
+  for (int k = 0; k < CGKS_PJ_IN; ++k) {
+    double col[10];
+    if (bnd && k >= 20 && k < 40) {
+#pragma unroll
+      for (int o = 0; o < 10; ++o) col[o] = 0.0;
+    } else {
+      DualD WL[5], GL[15], WR[5], GR[15], Fg[5], Wg[5], al;
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        WL[q] = DualD(p.WL[q], k == q ? 1.0 : 0.0);
+        WR[q] = DualD(bnd ? 0.0 : p.WR[q], k == 20 + q ? 1.0 : 0.0);
+      }
+#pragma unroll
+      for (int j = 0; j < 15; ++j) {
+        GL[j] = DualD(p.GL[j], k == 5 + j ? 1.0 : 0.0);
+        GR[j] = DualD(bnd ? 0.0 : p.GR[j], k == 25 + j ? 1.0 : 0.0);
+      }
+      const DualD dtf(p.dtf, k == 40 ? 1.0 : 0.0);
+      point_flux<DualD>(p.n, p.iw, bnd, tag, WL, GL, WR, GR, dtf, a.ph, Fg, Wg, al, a.err, p.f);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        col[q] = Fg[q].d;
+        col[5 + q] = Wg[q].d;
+      }
+    }
+#pragma unroll
+    for (int o = 0; o < 10; ++o) Jp[(int64_t)(10 * k + o) * ngp + g] = col[o];
+  }
 }
 
 struct GatherArgs {

@@ -106,6 +106,16 @@ struct cgks_ctx {
   int64_t* d_skipped = nullptr;     // coarse updates and corrections skipped by the positivity rule
   double r1 = 0.0;
   int64_t iters = 0;
+  // adjoint: the stored linearisation at the state of the last cgks_linearize, its time steps,
+  // and the work arrays of the transposed products (in mesh_allocs)
+  double *Jp = nullptr, *Jr = nullptr, *adt = nullptr;
+  double *pbar = nullptr, *aself = nullptr, *arec = nullptr, *avec = nullptr, *apart = nullptr;
+  bool linearized = false;
+  // host copy of the uploaded mesh (shape derivatives re-upload it with displaced nodes)
+  std::vector<double> h_xyz;
+  std::vector<int8_t> h_ctype;
+  std::vector<int64_t> h_cptr, h_bptr;
+  std::vector<int32_t> h_cnodes, h_bnodes, h_btag, h_pairs;
   std::vector<void*> mesh_allocs;   // freed on re-upload / destroy
   std::vector<void*> ctx_allocs;    // freed on destroy
   // kernel timing (cgks_profile): event pairs per fine kernel kind

@@ -92,6 +92,61 @@ HD Dual<float> tpow<Dual<float>>(Dual<float> x, Dual<float> y) {  // y constant
   return {p, y.v * p / x.v * x.d};
 }
 
+// Dual<double>: the forward-mode linearisation of the FP64 residual.  Mixed operations with
+// double constants, comparisons on values, and the elementary functions the residual calls (the
+// derivative of each from its closed form: erfc' = -2/sqrt(pi) exp(-x^2)).  At the kinks the
+// residual meets exactly (|x| at x = 0, fmin at equal arguments: a velocity component that is zero
+// in a uniform stream, equal indicators in uniform regions) the derivative is the mean of the two
+// one-sided ones, which is what a central difference measures: |x|' = 0 at 0, fmin' = the mean.
+using DualD = Dual<double>;
+HD DualD operator+(DualD a, double b) { return {a.v + b, a.d}; }
+HD DualD operator+(double a, DualD b) { return {a + b.v, b.d}; }
+HD DualD operator-(DualD a, double b) { return {a.v - b, a.d}; }
+HD DualD operator-(double a, DualD b) { return {a - b.v, -b.d}; }
+HD DualD operator*(DualD a, double b) { return {a.v * b, a.d * b}; }
+HD DualD operator*(double a, DualD b) { return {a * b.v, a * b.d}; }
+HD DualD operator/(DualD a, double b) { return {a.v / b, a.d / b}; }
+HD DualD operator/(double a, DualD b) {
+  const double q = a / b.v;
+  return {q, -q * b.d / b.v};
+}
+HD DualD& operator+=(DualD& a, double b) { return a = a + b; }
+HD DualD& operator-=(DualD& a, DualD b) { return a = a - b; }
+HD DualD& operator*=(DualD& a, DualD b) { return a = a * b; }
+HD DualD& operator*=(DualD& a, double b) { return a = a * b; }
+HD bool operator>(DualD a, double b) { return a.v > b; }
+HD bool operator<(DualD a, double b) { return a.v < b; }
+HD bool operator>=(DualD a, double b) { return a.v >= b; }
+HD bool operator<=(DualD a, double b) { return a.v <= b; }
+HD bool operator!=(DualD a, double b) { return a.v != b; }
+HD DualD sqrt(DualD x) {
+  const double r = sqrt(x.v);
+  return {r, 0.5 * x.d / r};
+}
+HD DualD exp(DualD x) {
+  const double e = exp(x.v);
+  return {e, e * x.d};
+}
+HD DualD erfc(DualD x) { return {erfc(x.v), -1.1283791670955125739 * exp(-x.v * x.v) * x.d}; }
+HD DualD fabs(DualD x) { return {fabs(x.v), x.v < 0.0 ? -x.d : (x.v > 0.0 ? x.d : 0.0)}; }
+HD DualD fmin(DualD a, DualD b) {
+  if (a.v == b.v) return {a.v, 0.5 * (a.d + b.d)};
+  return b.v < a.v ? b : a;
+}
+HD DualD pow(DualD x, double y) {
+  const double p = pow(x.v, y);
+  return {p, y * p / x.v * x.d};
+}
+HD bool isfinite(DualD x) { return isfinite(x.v); }
+template <>
+HD DualD tsqrt<DualD>(DualD x) { return sqrt(x); }
+template <>
+HD DualD texp<DualD>(DualD x) { return exp(x); }
+template <>
+HD DualD terfc<DualD>(DualD x) { return erfc(x); }
+template <>
+HD DualD tpow<DualD>(DualD x, DualD y) { return pow(x, y.v); }  // y constant
+
 // branchless orthonormal basis (t1, t2) completing the unit normal n (Duff et al., JCGT 6(1), 2017)
 template <typename T>
 HD void face_frame(const T n[3], T t1[3], T t2[3]) {

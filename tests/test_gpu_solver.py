@@ -185,7 +185,13 @@ def test_error_paths(cg):
     with pytest.raises(cg.CgksError) as e:
         ctx.step(1)
     assert e.value.status == 5 and "index" in str(e.value)
-    assert cg.load().cgks_adjoint(ctx.h, None, 0, None, None) == 8
+    # the adjoint needs the compression factor off (it is on by default)
+    with pytest.raises(cg.CgksError) as e:
+        ctx.linearize()
+    assert e.value.status == 8
+    with pytest.raises(cg.CgksError) as e:
+        ctx.adjoint(1)
+    assert e.value.status == 8
     ctx.close()
 
 
