@@ -275,6 +275,130 @@ def run_scale(args):
                       "scale": rows}))
 
 
+ADJ_WORKLOAD = dict(nx=160, ny=80, nz=80, n_prism=8)
+ADJ_SMALL = dict(nx=64, ny=32, nz=8, n_prism=4)
+
+
+def _steady(ctx, chunk=200, max_steps=200000):
+    """Single-grid steps until the density-residual norm stops falling at round-off."""
+    steps, last = 0, float("inf")
+    while steps < max_steps:
+        h = ctx.step(chunk)
+        steps += chunk
+        if h[-1] < 1e-10 and h.min() > 0.9 * last:
+            break
+        last = min(last, h.min())
+    return steps, float(h[-1])
+
+
+def run_adjoint(args):
+    """The discrete adjoint (an extension of the method): (1) on the Mach-3 compression ramp at
+    160 x 80 x 80 with 8 prism layers (1,126,400 cells) the time of forming the stored linearisation
+    and of one transposed product (the three kernels of each adjoint iteration) with its HBM bytes;
+    (2) on the same ramp at 64 x 32 x 8 the whole gradient of the wall force in the Mach number and 64
+    wall modes at the steady state, with the phases timed and dJ/dMach checked against central
+    differences of the converged functional."""
+    import numpy as np
+    import torch
+    import meshgen as mg
+    import paper_2402_02075_gb300 as cg
+    prm = dict(mach=3.0, n_levels=1, compression_factor=0)
+    out = {"metric": "adjoint: transposed-product HBM GB/s; gradient wall time", "n_gpus": 1, "dtype": "f64",
+           "data": "synthetic (seeded ramp meshes, free-stream start)"}
+    # (1) full size
+    w = ADJ_WORKLOAD
+    mesh = mg.ramp_box(w["nx"], w["ny"], w["nz"], n_prism=w["n_prism"])
+    ctx = cg.upload_mesh(mesh, cg.default_params(**prm))
+    nc = ctx.nc
+    W, G = mg.uniform_state(nc, mach=3.0)
+    ctx.state_init(torch.from_numpy(W).cuda(), torch.from_numpy(G).cuda(), torch.ones(nc, dtype=torch.float64, device="cuda"))
+    ctx.step(20, history=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.linearize()
+    torch.cuda.synchronize()
+    t_lin = time.perf_counter() - t0
+    nf = ctx.level_info(0)[1]
+    ngp = mg_gauss_points(mesh)
+    rb = torch.randn(5, nc, dtype=torch.float64, device="cuda")
+    gb = torch.randn(15, nc, dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        ctx.residual_vjp(rb, gb)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(ctx.stream)
+    for _ in range(args.steps):
+        ctx.residual_vjp(rb, gb)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    # bytes of one product: the stored matrices (41 x 10 per point, 140 x 51 per cell), the point
+    # cotangents written and read, the neighbour records written and read, the cell vectors in/out
+    by = 8 * (410 * ngp + 7140 * nc + 2 * 41 * ngp + 3 * ngp + 2 * 40 * nf + 2 * 20 * nc + 3 * 20 * nc)
+    peak = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak = json.load(f).get("hbm_gbs")
+    except (OSError, ValueError):
+        pass
+    out["full"] = {"workload": f"ramp {w['nx']}x{w['ny']}x{w['nz']}, {w['n_prism']} prism layers", "cells": nc,
+                   "faces": nf, "gauss_points": ngp, "linearize_s": t_lin, "vjp_ms": ms,
+                   "stored_linearisation_GB": 8 * (410 * ngp + 7140 * nc) / 1e9,
+                   "vjp_bytes_GB": by / 1e9, "vjp_GBps": by / (ms * 1e-3) / 1e9, "hbm_peak_GBps": peak,
+                   "frac": (by / (ms * 1e-3) / 1e9) / peak if peak else None}
+    ctx.close()
+    del mesh
+    torch.cuda.empty_cache()
+    # (2) whole gradient at a steady state
+    w = ADJ_SMALL
+    mesh = mg.ramp_box(w["nx"], w["ny"], w["nz"], n_prism=w["n_prism"])
+    ctx = cg.upload_mesh(mesh, cg.default_params(**prm))
+    nc = ctx.nc
+    W, G = mg.uniform_state(nc, mach=3.0)
+    Wd, Gd, ad = torch.from_numpy(W).cuda(), torch.from_numpy(G).cuda(), torch.ones(nc, dtype=torch.float64, device="cuda")
+    ctx.state_init(Wd, Gd, ad)
+    t0 = time.perf_counter()
+    steps, res = _steady(ctx)
+    t_primal = time.perf_counter() - t0
+    modes = mg.ramp_wall_modes(mesh, 64)
+    t0 = time.perf_counter()
+    g = ctx.adjoint(1, modes, tol=1e-10)
+    t_adj = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    g0 = ctx.adjoint(1, None, tol=1e-10)
+    t_adj_mach = time.perf_counter() - t0
+    Ws, Gs, _ = ctx.state_get()
+    J = []
+    for s in (1.0, -1.0):
+        c = cg.upload_mesh(mesh, cg.default_params(**dict(prm, mach=3.0 + s * 1e-6)))
+        c.state_init(Ws, Gs, ad)
+        _steady(c)
+        J.append(c.wall_force(1))
+        c.close()
+    fd = (J[0] - J[1]) / 2e-6
+    out["gradient"] = {"workload": f"ramp {w['nx']}x{w['ny']}x{w['nz']}, {w['n_prism']} prism layers", "cells": nc,
+                       "primal_steps": steps, "primal_final_norm": res, "primal_s": t_primal,
+                       "adjoint_iters": g["iters"], "adjoint_rel_res": g["rel_res"],
+                       "gradient_64_modes_and_mach_s": t_adj, "gradient_mach_only_s": t_adj_mach,
+                       "dJ_dmach": g["dJ_dmach"], "dJ_dmach_fd": fd,
+                       "dJ_dmach_rel_err": abs(g["dJ_dmach"] - fd) / abs(fd),
+                       "dJ_dmodes_first4": [float(x) for x in g["dJ_dmodes"][:4]]}
+    ctx.close()
+    print(json.dumps(out))
+
+
+def mg_gauss_points(mesh):
+    """Gauss points of a mesh dict (3 per triangular face, 4 per quadrilateral, each face once): the
+    cells' face slots count interior and periodic faces twice and the other boundary faces once."""
+    import numpy as np
+    pts = {4: 4 * 3, 5: 2 * 3 + 3 * 4, 6: 6 * 4, 7: 4 + 4 * 3}
+    t = np.asarray(mesh["cell_type"])
+    slots = sum(int((t == k).sum()) * v for k, v in pts.items())
+    bn = np.diff(np.asarray(mesh["bface_ptr"]))
+    bnd = np.asarray(mesh["bface_tag"]) < 100
+    return (slots + int(np.where(bn[bnd] == 3, 3, 4).sum())) // 2
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -316,12 +440,17 @@ def main():
     ap.add_argument("--no-converge", action="store_true")
     ap.add_argument("--size", default="full", choices=["full", "small"],
                     help="small: the same layout at 48x32x32 (profiling captures only)")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="adjoint measurements (stored linearisation, transposed product, gradient) instead")
     ap.add_argument("--scale", action="store_true",
                     help="scale sweep at 1.0M / 5.0M / 20.0M cells instead of the benchmark line")
     args = ap.parse_args()
     global WORKLOAD
     if args.scale:
         run_scale(args)
+        return
+    if args.adjoint:
+        run_adjoint(args)
         return
     if args.size == "small":
         WORKLOAD = dict(nx=48, ny=32, nz=32)
