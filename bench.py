@@ -332,9 +332,10 @@ def run_adjoint(args):
     e1.record(ctx.stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    # bytes of one product: the stored matrices (41 x 10 per point, 140 x 51 per cell), the point
-    # cotangents written and read, the neighbour records written and read, the cell vectors in/out
-    by = 8 * (410 * ngp + 7140 * nc + 2 * 41 * ngp + 3 * ngp + 2 * 40 * nf + 2 * 20 * nc + 3 * 20 * nc)
+    # bytes of one product: the stored matrices (41 x 10 per point; per cell 20 x 51 for its own
+    # slot and 6 x 200 for the neighbour slots), the point cotangents written and read, the point
+    # geometry, the neighbour records written and read, the cell vectors in and out
+    by = 8 * (410 * ngp + 2220 * nc + 2 * 41 * ngp + 3 * ngp + 2 * 40 * nf + 2 * 20 * nc + 3 * 20 * nc)
     peak = None
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -343,7 +344,7 @@ def run_adjoint(args):
         pass
     out["full"] = {"workload": f"ramp {w['nx']}x{w['ny']}x{w['nz']}, {w['n_prism']} prism layers", "cells": nc,
                    "faces": nf, "gauss_points": ngp, "linearize_s": t_lin, "vjp_ms": ms,
-                   "stored_linearisation_GB": 8 * (410 * ngp + 7140 * nc) / 1e9,
+                   "stored_linearisation_GB": 8 * (410 * ngp + 2220 * nc) / 1e9,
                    "vjp_bytes_GB": by / 1e9, "vjp_GBps": by / (ms * 1e-3) / 1e9, "hbm_peak_GBps": peak,
                    "frac": (by / (ms * 1e-3) / 1e9) / peak if peak else None}
     ctx.close()

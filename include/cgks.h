@@ -198,7 +198,7 @@ cgks_status cgks_skipped_updates(cgks_ctx* ctx, int64_t* count);
  * grad W, in the layouts of cgks_state_init. */
 
 /* Forms and stores the linearisation of (Res, Gnew) at the current state by forward-mode duals
- * (41 x 10 doubles per Gauss point, 140 x 51 per cell; device memory owned by the context, freed with
+ * (41 x 10 doubles per Gauss point, 2,220 per cell; device memory owned by the context, freed with
  * the mesh).  Errors: CGKS_EINVAL (no state), CGKS_ENOMEM, CGKS_EUNSUPPORTED. */
 cgks_status cgks_linearize(cgks_ctx* ctx);
 

@@ -9,7 +9,8 @@
 // of the face) -> fixed-order sums per cell.  cgks_linearize forms the Jacobian of each link by
 // forward-mode duals (the residual's own code on Dual<double>, exact to round-off) and keeps it:
 //   Jp [41 x 10][ngp]   per Gauss point
-//   Jr [140 x 51][nc]   per cell (7 stencil slots x 20 inputs; 50 coefficients and dt)
+//   Jr [2,220][nc]      per cell: own slot 20 inputs x (50 coefficients, dt); each of up to 6
+//                       neighbour slots 5 variables x 4 inputs x 10 coefficients (block diagonal)
 // so a transposed product is three memory-bound passes over stored matrices instead of a
 // reverse sweep through the flux (about 3.4 kFLOP of FP64 per point).  The transposed product runs
 // the chain backwards:
@@ -116,25 +117,32 @@ __global__ void __launch_bounds__(128) k_vjp_recon(VjpArgs a) {
       cb[CGKS_RC] += w_dt * a.pbar[(int64_t)40 * ngp + g];
     }
   }
-  // slot cotangents: self (slot 0) and one record per interior face for the cell across it
-  for (int s = 0; s <= nt; ++s) {
-    int64_t f = -1;
-    int side = 0;
-    if (s > 0) {
-      f = a.cf[(int64_t)(s - 1) * nc + i];
-      side = a.cside[(int64_t)(s - 1) * nc + i];
-      if (a.fR[f] < 0) continue;
-    }
-    for (int c = 0; c < 20; ++c) {
-      const int k = 20 * s + c;
-      const double* J = a.Jr + (int64_t)(CGKS_RJ_OUT * k) * nc + i;
-      double v = 0.0;
-#pragma unroll 3
-      for (int o = 0; o < CGKS_RJ_OUT; ++o) v += J[(int64_t)o * nc] * cb[o];
-      if (s == 0)
-        a.self[(int64_t)c * nc + i] = v;
-      else
-        a.rec[(int64_t)c * 2 * nf + 2 * f + side] = v;
+  // own slot: dense 20 x 51
+#pragma unroll 1
+  for (int c = 0; c < 20; ++c) {
+    const double* J = a.Jr + (int64_t)(CGKS_RJ_OUT * c) * nc + i;
+    double v = 0.0;
+#pragma unroll
+    for (int o = 0; o < CGKS_RJ_OUT; ++o) v += J[(int64_t)o * nc] * cb[o];
+    a.self[(int64_t)c * nc + i] = v;
+  }
+  // one record per interior face for the cell across it: per variable, 4 inputs x 10 coefficients
+  for (int s = 1; s <= nt; ++s) {
+    const int64_t f = a.cf[(int64_t)(s - 1) * nc + i];
+    if (a.fR[f] < 0) continue;
+    const int side = a.cside[(int64_t)(s - 1) * nc + i];
+    double* rec = a.rec + 2 * f + side;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+#pragma unroll
+      for (int c4 = 0; c4 < 4; ++c4) {
+        const double* J = a.Jr + (int64_t)(CGKS_RJ_SELF + ((s - 1) * 5 + q) * 40 + 10 * c4) * nc + i;
+        double v = 0.0;
+#pragma unroll
+        for (int j = 0; j < 10; ++j) v += J[(int64_t)j * nc] * cb[10 * q + j];
+        const int c = c4 == 0 ? q : 5 + 3 * q + (c4 - 1);
+        rec[(int64_t)c * 2 * nf] = v;
+      }
     }
   }
 }
@@ -274,7 +282,7 @@ static cgks_status adjoint_buffers(cgks_ctx* ctx) {
   const Fine& F = ctx->F;
   auto& M = ctx->mesh_allocs;
   CKS(dalloc(ctx, M, &ctx->Jp, (size_t)CGKS_PJ_IN * CGKS_PJ_OUT * F.ngp));
-  CKS(dalloc(ctx, M, &ctx->Jr, (size_t)CGKS_RJ_IN * CGKS_RJ_OUT * F.nc));
+  CKS(dalloc(ctx, M, &ctx->Jr, (size_t)CGKS_RJ_ROWS * F.nc));
   CKS(dalloc(ctx, M, &ctx->adt, F.nc));
   CKS(dalloc(ctx, M, &ctx->pbar, (size_t)CGKS_PJ_IN * F.ngp));
   CKS(dalloc(ctx, M, &ctx->aself, (size_t)20 * F.nc));

@@ -18,12 +18,17 @@
 #include "internal.cuh"
 #include "kinetic.cuh"
 
-// sizes of the stored linearisation (the adjoint): inputs and outputs of one Gauss point, of one
-// cell's reconstruction (7 stencil slots x (W, grad W); the coefficients and the time step)
+// sizes of the stored linearisation (the adjoint): inputs and outputs of one Gauss point; of one
+// cell's reconstruction: its own slot dense (20 inputs (W, grad W) x 51 outputs, the coefficients and
+// the time step), and per neighbour slot (up to 6) one block per variable q, 4 inputs (W_q and its
+// gradient) x its 10 coefficients -- each variable is reconstructed on its own, so a neighbour's
+// variable q reaches no other variable's coefficients (only the cell's own ghosts couple them)
 #define CGKS_PJ_IN 41
 #define CGKS_PJ_OUT 10
-#define CGKS_RJ_IN 140
 #define CGKS_RJ_OUT 51
+#define CGKS_RJ_SELF (20 * CGKS_RJ_OUT)
+#define CGKS_RJ_NB (5 * 4 * 10)
+#define CGKS_RJ_ROWS (CGKS_RJ_SELF + 6 * CGKS_RJ_NB)
 
 HD double rsqrt_hd(double x) {
 #ifdef __CUDA_ARCH__
@@ -208,20 +213,18 @@ HD void reconstruct_body(int64_t i, const ReconArgs& a) {
   a.dt[i] = time_step<double>(i, a, Q0);
 }
 
-// forward-mode linearisation of the reconstruction of cell i: Jr[(51 k + o) nc + i] = d out_o /
-// d in_k, outputs o = (the 50 coefficients, the time step), inputs k = 20 s + c as in
-// reconstruct_cell for the 1 + 6 stencil slots; columns of absent slots (boundary faces, fewer
-// faces) are zero
+// forward-mode linearisation of the reconstruction of cell i into Jr [CGKS_RJ_ROWS][nc]: rows
+// 51 c + o of the own slot (input c of (W, grad W), output o of (50 coefficients, time step)), then
+// for neighbour slot s = 1..6 the rows CGKS_RJ_SELF + ((s - 1) 5 + q) 40 + 10 c4 + j: input c4 of
+// (W_q, d/dx, d/dy, d/dz of W_q), output coefficient j of variable q; absent slots (boundary faces,
+// fewer faces) are zero
 HD void recon_jacobian_body(int64_t i, const ReconArgs& a, double* Jr) {
   const int64_t nc = a.nc;
   const int nt = a.ctype[i] == 7 ? 5 : a.ctype[i];
-  for (int k = 0; k < CGKS_RJ_IN; ++k) {
-    const int slot = k / 20;
-    bool live = slot == 0;
-    if (slot >= 1 && slot <= nt) live = a.fR[a.cf[(int64_t)(slot - 1) * nc + i]] >= 0;
+  for (int k = 0; k < 20; ++k) {
     DualD out[CGKS_RC];
-    if (live) reconstruct_cell<DualD>(i, a, k, out);
-    for (int o = 0; o < CGKS_RC; ++o) Jr[(int64_t)(CGKS_RJ_OUT * k + o) * nc + i] = live ? out[o].d : 0.0;
+    reconstruct_cell<DualD>(i, a, k, out);
+    for (int o = 0; o < CGKS_RC; ++o) Jr[(int64_t)(CGKS_RJ_OUT * k + o) * nc + i] = out[o].d;
     double ddt = 0.0;
     if (k < 5) {
       DualD Q0[5];
@@ -229,6 +232,16 @@ HD void recon_jacobian_body(int64_t i, const ReconArgs& a, double* Jr) {
       ddt = time_step<DualD>(i, a, Q0).d;
     }
     Jr[(int64_t)(CGKS_RJ_OUT * k + CGKS_RC) * nc + i] = ddt;
+  }
+  for (int s = 1; s <= 6; ++s) {
+    const bool live = s <= nt && a.fR[a.cf[(int64_t)(s - 1) * nc + i]] >= 0;
+    for (int c = 0; c < 20; ++c) {
+      const int q = c < 5 ? c : (c - 5) / 3, c4 = c < 5 ? 0 : 1 + (c - 5) % 3;
+      DualD out[CGKS_RC];
+      if (live) reconstruct_cell<DualD>(i, a, 20 * s + c, out);
+      const int64_t row = CGKS_RJ_SELF + ((s - 1) * 5 + q) * 40 + 10 * c4;
+      for (int j = 0; j < 10; ++j) Jr[(row + j) * nc + i] = live ? out[10 * q + j].d : 0.0;
+    }
   }
 }
 
