@@ -23,6 +23,11 @@
 // All sums run in a fixed order (no atomics), so results are reproducible bit for bit.
 #include "fine.cuh"
 
+// point cotangents are one record per Gauss point (41 values padded to 42 doubles, 336 bytes: the
+// per-cell kernel gathers its faces' points, so each reads 21 contiguous 16-byte pairs instead of 41
+// scattered words); neighbour records are one 20-double record per face side
+#define CGKS_PB 42
+
 // ---- forward-mode linearisation ----------------------------------------------------------------
 
 __global__ void __launch_bounds__(128) k_point_jac(PointArgs a, double* Jp) {
@@ -43,7 +48,7 @@ struct VjpArgs {
   const int32_t *cf, *fL, *fR, *gp_face, *gp_ptr;
   const double *gp_x, *gp_A, *fshift, *ctr, *vol, *dt, *Jp, *Jr;
   const double *rbar, *gbar;  // cotangents of Res [5][nc] and Gnew [15][nc]
-  double *pbar, *self, *rec;  // [41][ngp], [20][nc], [20][2 nf]
+  double *pbar, *self, *rec;  // [ngp][42] (41 used), [20][nc], [2 nf][20]
   double *out;                // [20][nc]: cotangents of (W, G)
 };
 
@@ -70,7 +75,7 @@ __global__ void __launch_bounds__(128) k_vjp_points(VjpArgs a) {
     double s = 0.0;
 #pragma unroll
     for (int o = 0; o < CGKS_PJ_OUT; ++o) s += J[(int64_t)o * ngp] * ub[o];
-    a.pbar[(int64_t)k * ngp + g] = s;
+    a.pbar[(int64_t)g * CGKS_PB + k] = s;
   }
 }
 
@@ -95,12 +100,17 @@ __global__ void __launch_bounds__(128) k_vjp_recon(VjpArgs a) {
       double X[3];
 #pragma unroll
       for (int d = 0; d < 3; ++d) X[d] = a.gp_x[d * ngp + g] - (side ? a.fshift[d * nf + f] : 0.0) - a.ctr[d * nc + i];
+      const double2* pb2 = reinterpret_cast<const double2*>(a.pbar + (int64_t)g * CGKS_PB + base);
+      double pb[20];
+#pragma unroll
+      for (int k = 0; k < 10; ++k) {
+        const double2 v = pb2[k];
+        pb[2 * k] = v.x;
+        pb[2 * k + 1] = v.y;
+      }
 #pragma unroll
       for (int q = 0; q < 5; ++q) {
-        const double w = a.pbar[(int64_t)(base + q) * ngp + g];
-        const double gx = a.pbar[(int64_t)(base + 5 + 3 * q) * ngp + g];
-        const double gy = a.pbar[(int64_t)(base + 6 + 3 * q) * ngp + g];
-        const double gz = a.pbar[(int64_t)(base + 7 + 3 * q) * ngp + g];
+        const double w = pb[q], gx = pb[5 + 3 * q], gy = pb[6 + 3 * q], gz = pb[7 + 3 * q];
         // basis 1, X, Y, Z, X^2, Y^2, Z^2, XY, YZ, XZ and its gradient
         double* c = cb + 10 * q;
         c[0] += w;
@@ -114,7 +124,7 @@ __global__ void __launch_bounds__(128) k_vjp_recon(VjpArgs a) {
         c[8] += w * X[1] * X[2] + X[2] * gy + X[1] * gz;
         c[9] += w * X[0] * X[2] + X[2] * gx + X[0] * gz;
       }
-      cb[CGKS_RC] += w_dt * a.pbar[(int64_t)40 * ngp + g];
+      cb[CGKS_RC] += w_dt * a.pbar[(int64_t)g * CGKS_PB + 40];
     }
   }
   // own slot: dense 20 x 51
@@ -131,7 +141,7 @@ __global__ void __launch_bounds__(128) k_vjp_recon(VjpArgs a) {
     const int64_t f = a.cf[(int64_t)(s - 1) * nc + i];
     if (a.fR[f] < 0) continue;
     const int side = a.cside[(int64_t)(s - 1) * nc + i];
-    double* rec = a.rec + 2 * f + side;
+    double r[20];
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
 #pragma unroll
@@ -140,17 +150,19 @@ __global__ void __launch_bounds__(128) k_vjp_recon(VjpArgs a) {
         double v = 0.0;
 #pragma unroll
         for (int j = 0; j < 10; ++j) v += J[(int64_t)j * nc] * cb[10 * q + j];
-        const int c = c4 == 0 ? q : 5 + 3 * q + (c4 - 1);
-        rec[(int64_t)c * 2 * nf] = v;
+        r[c4 == 0 ? q : 5 + 3 * q + (c4 - 1)] = v;
       }
     }
+    double2* rec = reinterpret_cast<double2*>(a.rec + (2 * f + side) * 20);
+#pragma unroll
+    for (int k = 0; k < 10; ++k) rec[k] = make_double2(r[2 * k], r[2 * k + 1]);
   }
 }
 
 __global__ void __launch_bounds__(128) k_vjp_cells(VjpArgs a) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= a.nc) return;
-  const int64_t nc = a.nc, nf = a.nf;
+  const int64_t nc = a.nc;
   const int nt = a.ctype[i] == 7 ? 5 : a.ctype[i];
   double v[20];
 #pragma unroll
@@ -159,8 +171,13 @@ __global__ void __launch_bounds__(128) k_vjp_cells(VjpArgs a) {
     const int64_t f = a.cf[(int64_t)m * nc + i];
     if (a.fR[f] < 0) continue;
     const int other = 1 - a.cside[(int64_t)m * nc + i];
+    const double2* rec = reinterpret_cast<const double2*>(a.rec + (2 * f + other) * 20);
 #pragma unroll
-    for (int c = 0; c < 20; ++c) v[c] += a.rec[(int64_t)c * 2 * nf + 2 * f + other];
+    for (int k = 0; k < 10; ++k) {
+      const double2 r = rec[k];
+      v[2 * k] += r.x;
+      v[2 * k + 1] += r.y;
+    }
   }
 #pragma unroll
   for (int c = 0; c < 20; ++c) a.out[(int64_t)c * nc + i] = v[c];
@@ -284,7 +301,7 @@ static cgks_status adjoint_buffers(cgks_ctx* ctx) {
   CKS(dalloc(ctx, M, &ctx->Jp, (size_t)CGKS_PJ_IN * CGKS_PJ_OUT * F.ngp));
   CKS(dalloc(ctx, M, &ctx->Jr, (size_t)CGKS_RJ_ROWS * F.nc));
   CKS(dalloc(ctx, M, &ctx->adt, F.nc));
-  CKS(dalloc(ctx, M, &ctx->pbar, (size_t)CGKS_PJ_IN * F.ngp));
+  CKS(dalloc(ctx, M, &ctx->pbar, (size_t)CGKS_PB * F.ngp));
   CKS(dalloc(ctx, M, &ctx->aself, (size_t)20 * F.nc));
   CKS(dalloc(ctx, M, &ctx->arec, (size_t)20 * 2 * F.nf));
   // work vectors: mu, v, wbar, g, lambda, F+, F- (20 rows each) and one row of per-cell scalars
