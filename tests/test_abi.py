@@ -46,4 +46,10 @@ def test_context_free_checks_need_no_device(lib):
     assert L.cgks_default_params(None) == 1
     assert L.cgks_destroy(None) == 0
     assert L.cgks_density_norm_noalloc(None, None, 10, None, None) == 1
+    # the adjoint entry points refuse a NULL context before any device work
+    assert L.cgks_linearize(None) == 1
+    assert L.cgks_residual_vjp(None, None, None, None, None) == 1
+    assert L.cgks_wall_force(None, 1, None, None) == 1
+    assert L.cgks_adjoint_solve(None, None, 10, 1e-10, None, None, None) == 1
+    assert L.cgks_adjoint(None, 1, None, 0, 1e-6, 1e-6, 10, 1e-10, None, None, None, None) == 1
     assert b"NULL" in L.cgks_last_error(None)
