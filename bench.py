@@ -368,6 +368,7 @@ def run_adjoint(args):
     t0 = time.perf_counter()
     g0 = ctx.adjoint(1, None, tol=1e-10)
     t_adj_mach = time.perf_counter() - t0
+
     Ws, Gs, _ = ctx.state_get()
     J = []
     for s in (1.0, -1.0):
@@ -381,6 +382,7 @@ def run_adjoint(args):
                        "primal_steps": steps, "primal_final_norm": res, "primal_s": t_primal,
                        "adjoint_iters": g["iters"], "adjoint_rel_res": g["rel_res"],
                        "gradient_64_modes_and_mach_s": t_adj, "gradient_mach_only_s": t_adj_mach,
+                       "adjoint_solver": "transposed pseudo-time iteration",
                        "dJ_dmach": g["dJ_dmach"], "dJ_dmach_fd": fd,
                        "dJ_dmach_rel_err": abs(g["dJ_dmach"] - fd) / abs(fd),
                        "dJ_dmodes_first4": [float(x) for x in g["dJ_dmodes"][:4]]}

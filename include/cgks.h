@@ -213,26 +213,32 @@ cgks_status cgks_residual_vjp(cgks_ctx* ctx, const double* res_bar, const double
  * dJ_dW: NULLable device [5][N] out (dJ/dW, zero away from the wall).  Synchronises. */
 cgks_status cgks_wall_force(cgks_ctx* ctx, int component, double* J, double* dJ_dW);
 
-/* Solves (dF/du)^T lambda = -dJ_du with the stored linearisation by the transposed pseudo-time
- * iteration of the explicit scheme: mu <- mu + (dF/du)^T P mu + dJ_du, lambda = P mu, P the local
- * time steps over the volumes on the W rows (the iteration matrix is the transpose of the explicit
- * scheme's, so it converges where the scheme does).  dJ_du [20][N] in, lambda [20][N] out (device).
- * Stops when |(dF/du)^T lambda + dJ_du| <= tol |dJ_du| (checked every 25 iterations) or after
- * max_iters; iters and rel_res (NULLable host) report the count and the ratio.  Errors:
- * CGKS_ENOTCONV (tolerance not reached; lambda holds the last iterate), CGKS_ENAN (divergence). */
-cgks_status cgks_adjoint_solve(cgks_ctx* ctx, const double* dJ_du, int64_t max_iters, double tol, double* lambda,
-                               int64_t* iters, double* rel_res);
+/* Solves (dF/du)^T lambda = -dJ_du with the stored linearisation, in the variable mu with
+ * lambda = P mu, P the local time steps over the volumes on the W rows (identity on the G rows):
+ *   method 0: the transposed pseudo-time iteration of the explicit scheme, mu <- mu + (dF/du)^T P mu
+ *             + dJ_du (its iteration matrix is the transpose of the scheme's, so it converges where
+ *             the scheme does; the residual is checked every 25 iterations);
+ *   method 1: restarted GMRES(30) on (dF/du)^T P mu = -dJ_du (30 Krylov vectors of [20][N] held on
+ *             the device, allocated on first use, freed with the mesh); fewer products than method
+ *             0 on small cases, but restarted GMRES can stagnate (it did on an 18,432-cell ramp).
+ * dJ_du [20][N] in, lambda [20][N] out (device).  Stops when |(dF/du)^T lambda + dJ_du| <= tol
+ * |dJ_du| or after max_iters transposed products; iters and rel_res (NULLable host) report the
+ * count and the ratio.  Errors: CGKS_EINVAL (bad method), CGKS_ENOTCONV (tolerance not reached;
+ * lambda holds the last iterate), CGKS_ENAN (divergence). */
+cgks_status cgks_adjoint_solve(cgks_ctx* ctx, const double* dJ_du, int method, int64_t max_iters, double tol,
+                               double* lambda, int64_t* iters, double* rel_res);
 
 /* Gradient of the wall force (component 0..2) at the current (steady) state with respect to the
  * free-stream Mach number and to n_modes node displacement modes: node_modes host
  * [n_modes][n_nodes][3] (the upload's node order; NULL when n_modes == 0), dJ_dmodes host [n_modes]
- * out, dJ_dmach host out.  Linearises, solves the adjoint (max_iters, tol as cgks_adjoint_solve),
+ * out, dJ_dmach host out.  Linearises, solves the adjoint (method, max_iters, tol as
+ * cgks_adjoint_solve),
  * and takes the parameter partials dF/dbeta, dJ/dbeta at the frozen state by central differences of
  * the residual with steps h_mach and h_mode (for a mode: the mesh re-uploaded with its nodes moved,
  * into a one-level context on the same stream).  Synchronises. */
 cgks_status cgks_adjoint(cgks_ctx* ctx, int component, const double* node_modes, int n_modes, double h_mode,
-                         double h_mach, int64_t max_iters, double tol, double* dJ_dmodes, double* dJ_dmach,
-                         int64_t* iters, double* rel_res);
+                         double h_mach, int method, int64_t max_iters, double tol, double* dJ_dmodes,
+                         double* dJ_dmach, int64_t* iters, double* rel_res);
 
 /* Measured FP64 fused-multiply-add throughput of the current device in TFLOP/s (host output),
  * from a register-resident FMA chain kernel; the roofline denominator of the FP64-bound kernels. */

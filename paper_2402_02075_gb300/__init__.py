@@ -77,8 +77,9 @@ def load(path: str = LIB_PATH):
             "cgks_linearize": [P],
             "cgks_residual_vjp": [P, d, d, d, d],
             "cgks_wall_force": [P, C.c_int, C.POINTER(C.c_double), d],
-            "cgks_adjoint_solve": [P, d, C.c_int64, C.c_double, d, C.POINTER(C.c_int64), C.POINTER(C.c_double)],
-            "cgks_adjoint": [P, C.c_int, d, C.c_int, C.c_double, C.c_double, C.c_int64, C.c_double, d,
+            "cgks_adjoint_solve": [P, d, C.c_int, C.c_int64, C.c_double, d, C.POINTER(C.c_int64),
+                                   C.POINTER(C.c_double)],
+            "cgks_adjoint": [P, C.c_int, d, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int64, C.c_double, d,
                              C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double)],
             "cgks_fp64_peak": [C.POINTER(C.c_double)],
             "cgks_profile": [P, C.c_int],
@@ -278,14 +279,17 @@ class Context:
         _check(load().cgks_wall_force(self.h, component, C.byref(J), _ptr(dJ)), self.h)
         return (J.value, dJ) if grad else J.value
 
-    def adjoint_solve(self, dJ_du, max_iters=100000, tol=1e-10):
+    def adjoint_solve(self, dJ_du, max_iters=100000, tol=1e-10, method=0):
+        """lambda of (dF/du)^T lambda = -dJ_du; method 0 transposed pseudo-time (the default: it
+        converges where the explicit scheme does), 1 restarted GMRES(30) (fewer products on small
+        cases, but it can stagnate)."""
         lam = self._empty(20, self.nc)
         it, rr = C.c_int64(), C.c_double()
-        _check(load().cgks_adjoint_solve(self.h, _ptr(dJ_du), max_iters, tol, _ptr(lam), C.byref(it), C.byref(rr)),
-               self.h)
+        _check(load().cgks_adjoint_solve(self.h, _ptr(dJ_du), method, max_iters, tol, _ptr(lam), C.byref(it),
+                                         C.byref(rr)), self.h)
         return lam, it.value, rr.value
 
-    def adjoint(self, component=1, modes=None, h_mode=1e-6, h_mach=1e-6, max_iters=100000, tol=1e-10):
+    def adjoint(self, component=1, modes=None, h_mode=1e-6, h_mach=1e-6, max_iters=100000, tol=1e-10, method=0):
         """dJ/dMach and dJ/d(mode amplitudes) of the wall force at the current steady state; modes:
         host float64 [n_modes][n_nodes][3] or None."""
         n = 0 if modes is None else len(modes)
@@ -293,8 +297,8 @@ class Context:
         out = np.zeros(max(n, 1))
         dm, it, rr = C.c_double(), C.c_int64(), C.c_double()
         _check(load().cgks_adjoint(self.h, component, None if md is None else md.ctypes.data_as(C.c_void_p), n, h_mode,
-                                   h_mach, max_iters, tol, out.ctypes.data_as(C.c_void_p), C.byref(dm), C.byref(it),
-                                   C.byref(rr)), self.h)
+                                   h_mach, method, max_iters, tol, out.ctypes.data_as(C.c_void_p), C.byref(dm),
+                                   C.byref(it), C.byref(rr)), self.h)
         return dict(dJ_dmach=dm.value, dJ_dmodes=out[:n], iters=it.value, rel_res=rr.value)
 
     def steady_solve(self, multigrid=True, drop=1e-10, max_iters=100000, raise_on_notconv=True):

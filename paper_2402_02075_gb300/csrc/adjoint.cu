@@ -21,6 +21,9 @@
 //                 cotangents of its own (W, G) and one record per neighbour
 //   k_vjp_cells   per cell: own part plus the records its neighbours wrote for it
 // All sums run in a fixed order (no atomics), so results are reproducible bit for bit.
+#include <algorithm>
+#include <vector>
+
 #include "fine.cuh"
 
 // point cotangents are one record per Gauss point (41 values padded to 42 doubles, 336 bytes: the
@@ -261,6 +264,30 @@ __global__ void k_adj_dot_rows(int64_t nc, const double* a, const double* bp, co
   x[i] = s;
 }
 
+// GMRES helpers over [20][nc] vectors: y = a x + b y; per-cell dot products d[i] = sum_c x y;
+// y = wbar - (0 on the W rows, x on the G rows) (the -I of Gnew - G)
+__global__ void k_axpby(int64_t n, double a, const double* x, double b, double* y) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k < n) y[k] = a * x[k] + b * y[k];
+}
+
+__global__ void k_dot_rows(int64_t nc, const double* x, const double* y, double* d) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nc) return;
+  double s = 0.0;
+  for (int c = 0; c < 20; ++c) s += x[(int64_t)c * nc + i] * y[(int64_t)c * nc + i];
+  d[i] = s;
+}
+
+__global__ void k_mv_finish(int64_t nc, const double* wbar, const double* x, double* y) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nc) return;
+  for (int c = 0; c < 20; ++c) {
+    const int64_t k = (int64_t)c * nc + i;
+    y[k] = wbar[k] - (c >= 5 ? x[k] : 0.0);
+  }
+}
+
 // fixed-order sum: 304 block partials over a grid-stride loop, then one block
 __global__ void k_sum_partial(int64_t n, const double* __restrict__ x, double* __restrict__ part) {
   __shared__ double s[256];
@@ -293,6 +320,8 @@ static cgks_status device_sum(cgks_ctx* ctx, const double* x, int64_t n, double*
   CK(cudaStreamSynchronize(ctx->stream));
   return CGKS_OK;
 }
+
+static constexpr int kGmresM = 30;  // Krylov vectors per restart
 
 static cgks_status adjoint_buffers(cgks_ctx* ctx) {
   if (ctx->pbar) return CGKS_OK;
@@ -379,11 +408,108 @@ cgks_status cgks_wall_force(cgks_ctx* ctx, int component, double* J, double* dJ_
   return check_device_error(ctx, "cgks_wall_force");
 }
 
-cgks_status cgks_adjoint_solve(cgks_ctx* ctx, const double* dJ_du, int64_t max_iters, double tol, double* lambda,
-                               int64_t* iters, double* rel_res) {
+// M x = (dF/du)^T P x: the operator of the adjoint system in the variable mu (lambda = P mu)
+static cgks_status adjoint_matvec(cgks_ctx* ctx, const double* x, double* y) {
+  const Fine& F = ctx->F;
+  const int64_t nc = F.nc;
+  double *v = ctx->avec + 20 * nc, *wbar = v + 20 * nc;
+  k_adj_scale<<<grid_for(nc, 128), 128, 0, ctx->stream>>>(nc, x, ctx->adt, F.vol, v);
+  CKS(run_vjp(ctx, v, x + 5 * nc, wbar));
+  k_mv_finish<<<grid_for(nc, 128), 128, 0, ctx->stream>>>(nc, wbar, x, y);
+  CK(cudaGetLastError());
+  return CGKS_OK;
+}
+
+static cgks_status dot(cgks_ctx* ctx, const double* x, const double* y, double* out) {
+  const int64_t nc = ctx->F.nc;
+  double* d = ctx->avec + 7 * 20 * nc;
+  k_dot_rows<<<grid_for(nc, 128), 128, 0, ctx->stream>>>(nc, x, y, d);
+  return device_sum(ctx, d, nc, out);
+}
+
+// restarted GMRES(kGmresM) on M mu = -g (modified Gram-Schmidt Arnoldi, Givens rotations); the
+// residual it reports is that of the adjoint system, |M mu + g| / |g|
+static cgks_status gmres(cgks_ctx* ctx, double* mu, const double* g, double gn, int64_t max_iters, double tol,
+                         int64_t* it_out, double* rel_out) {
+  const int64_t nc = ctx->F.nc, n = 20 * nc;
+  cudaStream_t st = ctx->stream;
+  double* V = ctx->akry;
+  const int m = kGmresM;
+  std::vector<double> H((m + 1) * m), cs(m), sn(m), sv(m + 1), yv(m);
+  int64_t it = 0;
+  double rel = 1.0;
+  bool first = true;
+  const unsigned gb = grid_for(n, 256);
+  for (;;) {
+    // true residual r = -g - M mu into V_0
+    if (first) {
+      k_axpby<<<gb, 256, 0, st>>>(n, -1.0, g, 0.0, V);
+    } else {
+      CKS(adjoint_matvec(ctx, mu, V));
+      ++it;
+      k_axpby<<<gb, 256, 0, st>>>(n, -1.0, g, -1.0, V);
+    }
+    first = false;
+    double b2 = 0.0;
+    CKS(dot(ctx, V, V, &b2));
+    const double beta = sqrt(b2);
+    rel = beta / gn;
+    if (!(rel <= 1e300)) return cgks_fail(ctx, CGKS_ENAN, "cgks_adjoint_solve: GMRES diverged");
+    if (rel <= tol || it >= max_iters) break;
+    k_axpby<<<gb, 256, 0, st>>>(n, 0.0, V, 1.0 / beta, V);
+    std::fill(sv.begin(), sv.end(), 0.0);
+    sv[0] = beta;
+    int k = 0;
+    for (int j = 0; j < m && it < max_iters; ++j) {
+      double* vj = V + (int64_t)j * n;
+      double* w = V + (int64_t)(j + 1) * n;
+      CKS(adjoint_matvec(ctx, vj, w));
+      ++it;
+      for (int i = 0; i <= j; ++i) {
+        double h = 0.0;
+        CKS(dot(ctx, w, V + (int64_t)i * n, &h));
+        H[i * m + j] = h;
+        k_axpby<<<gb, 256, 0, st>>>(n, -h, V + (int64_t)i * n, 1.0, w);
+      }
+      double w2 = 0.0;
+      CKS(dot(ctx, w, w, &w2));
+      const double hn = sqrt(w2);
+      H[(j + 1) * m + j] = hn;
+      if (hn > 0.0) k_axpby<<<gb, 256, 0, st>>>(n, 0.0, w, 1.0 / hn, w);
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * H[i * m + j] + sn[i] * H[(i + 1) * m + j];
+        H[(i + 1) * m + j] = -sn[i] * H[i * m + j] + cs[i] * H[(i + 1) * m + j];
+        H[i * m + j] = t;
+      }
+      const double den = hypot(H[j * m + j], H[(j + 1) * m + j]);
+      cs[j] = den > 0.0 ? H[j * m + j] / den : 1.0;
+      sn[j] = den > 0.0 ? H[(j + 1) * m + j] / den : 0.0;
+      H[j * m + j] = den;
+      H[(j + 1) * m + j] = 0.0;
+      sv[j + 1] = -sn[j] * sv[j];
+      sv[j] = cs[j] * sv[j];
+      k = j + 1;
+      if (fabs(sv[j + 1]) <= tol * gn || hn == 0.0) break;
+    }
+    // mu += V y with H y = s (upper triangular)
+    for (int i = k - 1; i >= 0; --i) {
+      double t = sv[i];
+      for (int l = i + 1; l < k; ++l) t -= H[i * m + l] * yv[l];
+      yv[i] = H[i * m + i] != 0.0 ? t / H[i * m + i] : 0.0;
+    }
+    for (int i = 0; i < k; ++i) k_axpby<<<gb, 256, 0, st>>>(n, yv[i], V + (int64_t)i * n, 1.0, mu);
+    CK(cudaGetLastError());
+  }
+  *it_out = it;
+  *rel_out = rel;
+  return CGKS_OK;
+}
+
+cgks_status cgks_adjoint_solve(cgks_ctx* ctx, const double* dJ_du, int method, int64_t max_iters, double tol,
+                               double* lambda, int64_t* iters, double* rel_res) {
   if (!ctx) return CGKS_EINVAL;
   if (!ctx->linearized) return cgks_fail(ctx, CGKS_EINVAL, "cgks_adjoint_solve: call cgks_linearize first");
-  if (!dJ_du || !lambda || max_iters < 1 || !(tol > 0.0))
+  if (!dJ_du || !lambda || max_iters < 1 || !(tol > 0.0) || (method != 0 && method != 1))
     return cgks_fail(ctx, CGKS_EINVAL, "cgks_adjoint_solve: bad arguments");
   const Fine& F = ctx->F;
   const int64_t nc = F.nc;
@@ -398,7 +524,12 @@ cgks_status cgks_adjoint_solve(cgks_ctx* ctx, const double* dJ_du, int64_t max_i
   const double gn = sqrt(g2);
   int64_t it = 0;
   double rel = 1.0;
-  if (gn > 0.0) {
+  if (!(gn > 0.0)) {
+    rel = 0.0;
+  } else if (method == 1) {
+    if (!ctx->akry) CKS(dalloc(ctx, ctx->mesh_allocs, &ctx->akry, (size_t)(kGmresM + 1) * 20 * nc));
+    CKS(gmres(ctx, mu, g, gn, max_iters, tol, &it, &rel));
+  } else {
     const int check = 25;
     while (it < max_iters) {
       k_adj_scale<<<grid_for(nc, 128), 128, 0, st>>>(nc, mu, ctx->adt, F.vol, v);
@@ -413,8 +544,6 @@ cgks_status cgks_adjoint_solve(cgks_ctx* ctx, const double* dJ_du, int64_t max_i
         if (rel <= tol) break;
       }
     }
-  } else {
-    rel = 0.0;
   }
   k_adj_lambda<<<grid_for(nc, 128), 128, 0, st>>>(nc, mu, ctx->adt, F.vol, v);
   CK(cudaMemcpyAsync(lambda, v, sizeof(double) * 20 * nc, cudaMemcpyDefault, st));
@@ -477,8 +606,8 @@ static cgks_status shape_partial(cgks_ctx* ctx, int component, const double* fie
 }
 
 cgks_status cgks_adjoint(cgks_ctx* ctx, int component, const double* node_modes, int n_modes, double h_mode,
-                         double h_mach, int64_t max_iters, double tol, double* dJ_dmodes, double* dJ_dmach,
-                         int64_t* iters, double* rel_res) {
+                         double h_mach, int method, int64_t max_iters, double tol, double* dJ_dmodes,
+                         double* dJ_dmach, int64_t* iters, double* rel_res) {
   CKS(adjoint_supported(ctx, "cgks_adjoint"));
   if (component < 0 || component > 2 || n_modes < 0 || (n_modes && (!node_modes || !dJ_dmodes || !(h_mode > 0.0))) ||
       !dJ_dmach || !(h_mach > 0.0))
@@ -493,7 +622,7 @@ cgks_status cgks_adjoint(cgks_ctx* ctx, int component, const double* node_modes,
   CKS(cgks_wall_force(ctx, component, &J, dJdu));
   CKS(cgks_linearize(ctx));
   double* lam_d = dJdu;  // the solve copies dJ/du out before it writes lambda here
-  CKS(cgks_adjoint_solve(ctx, dJdu, max_iters, tol, lam_d, iters, rel_res));
+  CKS(cgks_adjoint_solve(ctx, dJdu, method, max_iters, tol, lam_d, iters, rel_res));
   // Mach: the free stream (boundary states, viscosity) moves, the flow state stays
   double* Fpm[2] = {ctx->avec + 5 * 20 * nc, ctx->avec + 6 * 20 * nc};
   const cgks_params P0 = ctx->P;

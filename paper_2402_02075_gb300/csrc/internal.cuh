@@ -109,7 +109,7 @@ struct cgks_ctx {
   // adjoint: the stored linearisation at the state of the last cgks_linearize, its time steps,
   // and the work arrays of the transposed products (in mesh_allocs)
   double *Jp = nullptr, *Jr = nullptr, *adt = nullptr;
-  double *pbar = nullptr, *aself = nullptr, *arec = nullptr, *avec = nullptr, *apart = nullptr;
+  double *pbar = nullptr, *aself = nullptr, *arec = nullptr, *avec = nullptr, *apart = nullptr, *akry = nullptr;
   bool linearized = false;
   // host copy of the uploaded mesh (shape derivatives re-upload it with displaced nodes)
   std::vector<double> h_xyz;

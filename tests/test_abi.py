@@ -50,6 +50,6 @@ def test_context_free_checks_need_no_device(lib):
     assert L.cgks_linearize(None) == 1
     assert L.cgks_residual_vjp(None, None, None, None, None) == 1
     assert L.cgks_wall_force(None, 1, None, None) == 1
-    assert L.cgks_adjoint_solve(None, None, 10, 1e-10, None, None, None) == 1
-    assert L.cgks_adjoint(None, 1, None, 0, 1e-6, 1e-6, 10, 1e-10, None, None, None, None) == 1
+    assert L.cgks_adjoint_solve(None, None, 1, 10, 1e-10, None, None, None) == 1
+    assert L.cgks_adjoint(None, 1, None, 0, 1e-6, 1e-6, 1, 10, 1e-10, None, None, None, None) == 1
     assert b"NULL" in L.cgks_last_error(None)

@@ -213,3 +213,45 @@ def test_larger_ramp_mach_gradient_matches_converged_differences(cg):
     fd_m = _fd_converged(cg, prm, mesh, W, G)
     assert abs(g["dJ_dmach"] - fd_m) <= 1e-5 * abs(fd_m), (g["dJ_dmach"], fd_m)
     ctx.close()
+
+
+def test_gmres_and_pseudo_time_give_the_same_adjoint(ramp):
+    ctx, mesh, prm, W, G, modes, ref = ramp
+    J, dJ = ctx.wall_force(1, grad=True)
+    g = torch.zeros(20, ctx.nc, dtype=torch.float64, device="cuda")
+    g[:5] = dJ
+    ctx.linearize()
+    lam_k, it_k, rr_k = ctx.adjoint_solve(g, tol=1e-12, method=1)
+    lam_p, it_p, rr_p = ctx.adjoint_solve(g, tol=1e-12, method=0)
+    assert rr_k <= 1e-12 and rr_p <= 1e-12
+    assert it_k < it_p
+    a, b = lam_k.cpu().numpy(), lam_p.cpu().numpy()
+    assert np.abs(a - b).max() <= 1e-9 * np.abs(b).max()
+    # (lambda itself is not compared with the oracle's: at the steady state the linearisation has
+    # entries at near-ties of |U.n| where one-sided derivatives and the oracle's central differences
+    # differ; those directions do not reach the parameter gradients, which agree to 1e-6)
+
+
+def test_reupload_into_the_same_context(cg):
+    """The adjoint's arrays live with the mesh: a second upload into a context that has linearised
+    must give the same transposed product as a fresh context."""
+    big = mg.ramp_box(16, 8, 2, n_prism=1)
+    small = mg.periodic_box(4)
+    prm = dict(mach=0.5, n_levels=1, compression_factor=0)
+    ctx = cg.upload_mesh(big, cg.default_params(**prm))
+    W, G = mg.uniform_state(ctx.nc, mach=0.5)
+    ctx.state_init(_t(W), _t(G), _t(np.ones(ctx.nc)))
+    ctx.linearize()
+    ctx.mesh_upload(small)
+    rng = np.random.default_rng(4)
+    W, G = mg.uniform_state(ctx.nc, mach=0.5)
+    W = W * (1.0 + 0.02 * rng.standard_normal(W.shape))
+    G = 0.05 * rng.standard_normal(G.shape)
+    rb, gb = _t(rng.standard_normal((5, ctx.nc))), _t(rng.standard_normal((15, ctx.nc)))
+    outs = []
+    for c in (ctx, cg.upload_mesh(small, cg.default_params(**prm))):
+        c.state_init(_t(W), _t(G), _t(np.ones(c.nc)))
+        c.linearize()
+        outs.append([x.cpu().numpy() for x in c.residual_vjp(rb, gb)])
+        c.close()
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
