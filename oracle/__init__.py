@@ -5,8 +5,9 @@ tests, the smoke check and the benchmark's CPU-baseline leg to check and time th
 product library never imports, links or calls it, and it shares no code with the CUDA path.
 
 Functions without an independent pin ("parity unpinned" in the design notes): the Prandtl-number
-correction of the energy flux beyond its Pr = 1 reduction, the kinetic-weighted interface gradient
-of the equilibrium state, and the skewness limit value (the paper gives none).
+correction of the energy flux beyond its Pr = 1 reduction, the choice of the kinetic-weighted
+interface gradient of the equilibrium state (its half-space moment terms are pinned by quadrature;
+the paper prints no number for the reading), and the skewness limit value (the paper gives none).
 """
 from __future__ import annotations
 
@@ -98,6 +99,8 @@ def lib():
         _lib.orc_lusgs.argtypes = [P, C.c_int, d, d, d, d, C.POINTER(C.c_int64)]
         _lib.orc_pt_moments.argtypes = [d, C.c_double, C.c_int, d]
         _lib.orc_pt_slope.argtypes = [d, C.c_double, d, d]
+        _lib.orc_pt_mom_term.restype = C.c_double
+        _lib.orc_pt_mom_term.argtypes = [d, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, d, C.c_int]
         _lib.orc_pt_time.argtypes = [C.c_double, C.c_double, C.c_double, d]
         _lib.orc_pt_gks.argtypes = [C.POINTER(Params), d, d, d, d, d, C.c_double, d, d]
         _lib.orc_pt_kfvs.argtypes = [C.POINTER(Params), d, d, d, d]
@@ -308,6 +311,15 @@ def slope(rho, U, V, W, lam, K, dW):
     rc = lib().orc_pt_slope(_p(g, C.c_double), K, _p(dW, C.c_double), _p(s, C.c_double))
     assert rc == 0
     return s
+
+
+def mom_term(rho, U, V, W, lam, K, space, ku, kv, kw, s, alpha):
+    """int u^ku v^kv w^kw (s . psi) psi_alpha g over the full (0) or half (+1, -1) space; s None
+    for s . psi = 1."""
+    g = _f64([rho, U, V, W, lam])
+    sp = None if s is None else _f64(s)
+    return float(lib().orc_pt_mom_term(_p(g, C.c_double), K, space, ku, kv, kw,
+                                       None if sp is None else _p(sp, C.c_double), alpha))
 
 
 def time_integrals(dt, tau, tau_n):

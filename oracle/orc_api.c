@@ -284,6 +284,15 @@ void orc_pt_moments(const double* gp, double K, int space, double* out) {
   memcpy(out + 23, m.mxi, 3 * sizeof(double));
 }
 
+/* int u^ku v^kv w^kw (s . psi) psi_alpha g over the full (space 0) or half (+1 u > 0, -1 u < 0) space:
+ * the building block of every moment of the gas-kinetic flux (s NULL: s . psi := 1) */
+double orc_pt_mom_term(const double* gp, double K, int space, int ku, int kv, int kw, const double* s, int alpha) {
+  orc_maxw g = {gp[0], gp[1], gp[2], gp[3], gp[4]};
+  orc_mom m;
+  orc_moments(&g, K, space, &m);
+  return orc_mom_term(&m, ku, kv, kw, s, alpha);
+}
+
 int orc_pt_slope(const double* gp, double K, const double* dW, double* s) {
   orc_maxw g = {gp[0], gp[1], gp[2], gp[3], gp[4]};
   return orc_slope(&g, K, dW, s);

@@ -263,3 +263,34 @@ def test_sutherland_viscosity_enters_as_mu_of_the_interface_temperature(orc):
     np.testing.assert_allclose(Fs, Fe, rtol=1e-12, atol=1e-15)
     assert np.abs(Fs - F0).max() > 1e-6 * np.abs(F0).max()
     assert _sutherland(1.0, s) == 1.0
+
+
+def test_moment_terms_with_slopes_vs_brute_force(orc):
+    """The building block of every moment of the gas-kinetic flux, int u^a v^b w^c (s . psi) psi g
+    over the half spaces u > 0, u < 0 and the full space, for random Maxwellians and slopes s,
+    against product-rule quadrature (Gauss-Legendre in u, Gauss-Hermite elsewhere, K = 2).  This
+    pins, among others, the kinetic-weighted interface gradient sum_sides int_{side} psi (a . psi)
+    g_side and the interface state sum_sides int_{side} psi g_side."""
+    rng = np.random.default_rng(21)
+    K = 2
+    for _ in range(3):
+        rho, lam = 0.6 + 0.8 * rng.random(), 0.4 + 1.5 * rng.random()
+        U = rng.normal(size=3) * 0.8
+        s = rng.normal(size=5)
+        for space in (1, -1, 0):
+            if space:
+                coords, w = half_space_rule(rho, U, lam, K, space)
+            else:
+                coords, w = gauss_hermite_maxwellian(rho, U, lam, K, npts=8)
+            ps = psi(coords, K)
+            sp = s @ ps
+            for ku, kv, kw in ((0, 0, 0), (1, 0, 0), (2, 0, 0), (1, 1, 0), (1, 0, 1), (0, 1, 0)):
+                mono = coords[0] ** ku * coords[1] ** kv * coords[2] ** kw
+                for a in range(5):
+                    ref = float((mono * sp * ps[a]) @ w)
+                    scale = float((np.abs(mono * sp * ps[a])) @ w)
+                    got = orc.mom_term(rho, *U, lam, K, space, ku, kv, kw, s, a)
+                    assert abs(got - ref) <= 1e-11 * scale, (space, ku, kv, kw, a, got, ref)
+                    ref0 = float((mono * ps[a]) @ w)
+                    got0 = orc.mom_term(rho, *U, lam, K, space, ku, kv, kw, None, a)
+                    assert abs(got0 - ref0) <= 1e-11 * float(np.abs(mono * ps[a]) @ w)
