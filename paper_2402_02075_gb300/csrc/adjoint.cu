@@ -323,7 +323,16 @@ static cgks_status device_sum(cgks_ctx* ctx, const double* x, int64_t n, double*
 
 static constexpr int kGmresM = 30;  // Krylov vectors per restart
 
+// the functional's per-cell shares and the reduction partials (small: the wall force needs no more)
+static cgks_status small_buffers(cgks_ctx* ctx) {
+  if (ctx->ajc) return CGKS_OK;
+  CKS(dalloc(ctx, ctx->mesh_allocs, &ctx->apart, kSumParts + 1));
+  CKS(dalloc(ctx, ctx->mesh_allocs, &ctx->ajc, ctx->F.nc));
+  return CGKS_OK;
+}
+
 static cgks_status adjoint_buffers(cgks_ctx* ctx) {
+  CKS(small_buffers(ctx));
   if (ctx->pbar) return CGKS_OK;
   const Fine& F = ctx->F;
   auto& M = ctx->mesh_allocs;
@@ -335,7 +344,6 @@ static cgks_status adjoint_buffers(cgks_ctx* ctx) {
   CKS(dalloc(ctx, M, &ctx->arec, (size_t)20 * 2 * F.nf));
   // work vectors: mu, v, wbar, g, lambda, F+, F- (20 rows each) and one row of per-cell scalars
   CKS(dalloc(ctx, M, &ctx->avec, (size_t)(7 * 20 + 1) * F.nc));
-  CKS(dalloc(ctx, M, &ctx->apart, kSumParts + 1));
   return CGKS_OK;
 }
 
@@ -398,9 +406,9 @@ cgks_status cgks_wall_force(cgks_ctx* ctx, int component, double* J, double* dJ_
   if (!ctx) return CGKS_EINVAL;
   if (!ctx->has_mesh || !ctx->has_state) return cgks_fail(ctx, CGKS_EINVAL, "cgks_wall_force: no mesh or state");
   if (component < 0 || component > 2 || !J) return cgks_fail(ctx, CGKS_EINVAL, "cgks_wall_force: bad arguments");
-  CKS(adjoint_buffers(ctx));
+  CKS(small_buffers(ctx));
   const Fine& F = ctx->F;
-  double* jc = ctx->avec + 7 * 20 * F.nc;
+  double* jc = ctx->ajc;
   k_wall_force<<<grid_for(F.nc, 128), 128, 0, ctx->stream>>>(F.nc, F.ngp, F.ctype, F.cf, F.fR, F.ftag, F.gp_ptr, F.gp_A,
                                                              ctx->W, ctx->P.gamma, component, jc, dJ_dW);
   CK(cudaGetLastError());

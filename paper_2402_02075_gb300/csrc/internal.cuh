@@ -110,6 +110,7 @@ struct cgks_ctx {
   // and the work arrays of the transposed products (in mesh_allocs)
   double *Jp = nullptr, *Jr = nullptr, *adt = nullptr;
   double *pbar = nullptr, *aself = nullptr, *arec = nullptr, *avec = nullptr, *apart = nullptr, *akry = nullptr;
+  double* ajc = nullptr;  // per-cell shares of the wall force
   bool linearized = false;
   // host copy of the uploaded mesh (shape derivatives re-upload it with displaced nodes)
   std::vector<double> h_xyz;
