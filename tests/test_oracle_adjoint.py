@@ -51,3 +51,34 @@ def test_adjoint_solves_the_transposed_system(ramp):
     assert np.linalg.norm(A.T @ lam + g) <= 1e-10 * np.linalg.norm(g)
     # the steady problem is well posed: the linearisation is far from singular
     assert np.linalg.cond(A) < 1e10
+
+
+def test_wall_force_of_a_uniform_pressure_is_pressure_times_projected_area(orc):
+    """For a uniform pressure p the ramp's wall force in y is -p times the wall's projection on the
+    x-z plane, 2 x L_z (x from -0.5 to 1.5; the area vectors point out of the fluid, into the wall)."""
+    from oracle import adjoint as adj
+    for nx, ny, nz in ((8, 4, 2), (12, 6, 4)):
+        mesh = mg.ramp_box(nx, ny, nz, n_prism=1)
+        om = orc.Mesh(mesh)
+        W, _ = mg.uniform_state(om.nc, mach=3.0)
+        p = 1.0 / 1.4
+        Lz = nz * 2.0 / nx
+        assert abs(adj.wall_force(om, W, 1.4) - (-p * 2.0 * Lz)) <= 1e-12 * p * 2.0 * Lz
+        assert abs(adj.wall_force(om, W, 1.4, comp=2)) <= 1e-14
+
+
+def test_ramp_wall_modes_keep_periodic_copies_together_and_cells_valid(orc):
+    mesh = mg.ramp_box(16, 8, 4, n_prism=2)
+    modes = mg.ramp_wall_modes(mesh, 8)
+    xyz = mesh["xyz"]
+    ptr, nodes = mesh["bface_ptr"], mesh["bface_nodes"]
+    for a, b in np.asarray(mesh["periodic_pairs"]).reshape(-1, 2):
+        na, nb = nodes[ptr[a]:ptr[a + 1]], nodes[ptr[b]:ptr[b + 1]]
+        # each node of face a has a partner on face b at the same x, y
+        for i in na:
+            j = nb[np.argmin(np.abs(xyz[nb, 0] - xyz[i, 0]) + np.abs(xyz[nb, 1] - xyz[i, 1]))]
+            assert np.array_equal(modes[:, i], modes[:, j])
+    # amplitude 1e-3 (far above the differencing steps) leaves every cell with a positive volume
+    for m in modes:
+        vol = orc.Mesh(mg.displaced(mesh, m, 1e-3)).cells()[0]
+        assert vol.min() > 0.0
