@@ -16,20 +16,17 @@
 // the chain backwards:
 //   k_vjp_points  per point: cotangents of (flux, interface state) from those of (Res, Gnew) of
 //                 its two cells, times Jp^T -> cotangents of the point inputs
-//   k_vjp_recon   per cell: cotangents of its 50 coefficients and dt from its faces' points
-//                 (the transposed evaluation of the polynomial and its gradient), times Jr^T ->
-//                 cotangents of its own (W, G) and one record per neighbour
+//   k_vjp_coef    per cell: cotangents of its 50 coefficients and dt from its faces' points
+//                 (the transposed evaluation of the polynomial and its gradient)
+//   k_vjp_slots   per cell and row group: those times Jr^T -> cotangents of its own (W, G) and one
+//                 record per neighbour (32 cells x 16 groups per block, the cells' cotangents in
+//                 shared memory)
 //   k_vjp_cells   per cell: own part plus the records its neighbours wrote for it
 // All sums run in a fixed order (no atomics), so results are reproducible bit for bit.
 #include <algorithm>
 #include <vector>
 
-#include "fine.cuh"
-
-// point cotangents are one record per Gauss point (41 values padded to 42 doubles, 336 bytes: the
-// per-cell kernel gathers its faces' points, so each reads 21 contiguous 16-byte pairs instead of 41
-// scattered words); neighbour records are one 20-double record per face side
-#define CGKS_PB 42
+#include "adjoint.cuh"
 
 // ---- forward-mode linearisation ----------------------------------------------------------------
 
@@ -45,15 +42,6 @@ __global__ void __launch_bounds__(128) k_recon_jac(ReconArgs a, double* Jr) {
 
 // ---- transposed product ------------------------------------------------------------------------
 
-struct VjpArgs {
-  int64_t nc, nf, ngp;
-  const int8_t *ctype, *cside;
-  const int32_t *cf, *fL, *fR, *gp_face, *gp_ptr;
-  const double *gp_x, *gp_A, *fshift, *ctr, *vol, *dt, *Jp, *Jr;
-  const double *rbar, *gbar;  // cotangents of Res [5][nc] and Gnew [15][nc]
-  double *pbar, *self, *rec;  // [ngp][42] (41 used), [20][nc], [2 nf][20]
-  double *out;                // [20][nc]: cotangents of (W, G)
-};
 
 __global__ void __launch_bounds__(128) k_vjp_points(VjpArgs a) {
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -82,84 +70,21 @@ __global__ void __launch_bounds__(128) k_vjp_points(VjpArgs a) {
   }
 }
 
-__global__ void __launch_bounds__(128) k_vjp_recon(VjpArgs a) {
+__global__ void __launch_bounds__(128) k_vjp_coef(VjpArgs a) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < a.nc) vjp_coef_body(i, a);
+}
+
+// 32 cells x 16 row groups per block: the tile's 51 x 32 cotangents staged in shared memory once,
+// every row of the stored matrix read by a warp of 32 consecutive cells
+__global__ void __launch_bounds__(512) k_vjp_slots(VjpArgs a) {
+  __shared__ double cbs[CGKS_RJ_OUT][32];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int64_t i = blockIdx.x * (int64_t)32 + tx;
+  for (int o = ty; o < CGKS_RJ_OUT; o += 16) cbs[o][tx] = i < a.nc ? a.cbuf[(int64_t)o * a.nc + i] : 0.0;
+  __syncthreads();
   if (i >= a.nc) return;
-  const int64_t nc = a.nc, nf = a.nf, ngp = a.ngp;
-  const int nt = a.ctype[i] == 7 ? 5 : a.ctype[i];
-  double cb[CGKS_RJ_OUT];
-#pragma unroll
-  for (int o = 0; o < CGKS_RJ_OUT; ++o) cb[o] = 0.0;
-  for (int m = 0; m < nt; ++m) {
-    const int64_t f = a.cf[(int64_t)m * nc + i];
-    const int side = a.cside[(int64_t)m * nc + i];
-    const int64_t L = a.fL[f], R = a.fR[f];
-    const int base = side ? 20 : 0;
-    // the face time step is the smaller of the two cells' (shared equally at a tie, as a central
-    // difference of the minimum sees it)
-    const double own = side ? a.dt[R] : a.dt[L], other = side ? a.dt[L] : a.dt[R];
-    const double w_dt = R < 0 ? 1.0 : (own < other ? 1.0 : (own > other ? 0.0 : 0.5));
-    for (int64_t g = a.gp_ptr[f]; g < a.gp_ptr[f + 1]; ++g) {
-      double X[3];
-#pragma unroll
-      for (int d = 0; d < 3; ++d) X[d] = a.gp_x[d * ngp + g] - (side ? a.fshift[d * nf + f] : 0.0) - a.ctr[d * nc + i];
-      const double2* pb2 = reinterpret_cast<const double2*>(a.pbar + (int64_t)g * CGKS_PB + base);
-      double pb[20];
-#pragma unroll
-      for (int k = 0; k < 10; ++k) {
-        const double2 v = pb2[k];
-        pb[2 * k] = v.x;
-        pb[2 * k + 1] = v.y;
-      }
-#pragma unroll
-      for (int q = 0; q < 5; ++q) {
-        const double w = pb[q], gx = pb[5 + 3 * q], gy = pb[6 + 3 * q], gz = pb[7 + 3 * q];
-        // basis 1, X, Y, Z, X^2, Y^2, Z^2, XY, YZ, XZ and its gradient
-        double* c = cb + 10 * q;
-        c[0] += w;
-        c[1] += w * X[0] + gx;
-        c[2] += w * X[1] + gy;
-        c[3] += w * X[2] + gz;
-        c[4] += w * X[0] * X[0] + 2.0 * X[0] * gx;
-        c[5] += w * X[1] * X[1] + 2.0 * X[1] * gy;
-        c[6] += w * X[2] * X[2] + 2.0 * X[2] * gz;
-        c[7] += w * X[0] * X[1] + X[1] * gx + X[0] * gy;
-        c[8] += w * X[1] * X[2] + X[2] * gy + X[1] * gz;
-        c[9] += w * X[0] * X[2] + X[2] * gx + X[0] * gz;
-      }
-      cb[CGKS_RC] += w_dt * a.pbar[(int64_t)g * CGKS_PB + 40];
-    }
-  }
-  // own slot: dense 20 x 51
-#pragma unroll 1
-  for (int c = 0; c < 20; ++c) {
-    const double* J = a.Jr + (int64_t)(CGKS_RJ_OUT * c) * nc + i;
-    double v = 0.0;
-#pragma unroll
-    for (int o = 0; o < CGKS_RJ_OUT; ++o) v += J[(int64_t)o * nc] * cb[o];
-    a.self[(int64_t)c * nc + i] = v;
-  }
-  // one record per interior face for the cell across it: per variable, 4 inputs x 10 coefficients
-  for (int s = 1; s <= nt; ++s) {
-    const int64_t f = a.cf[(int64_t)(s - 1) * nc + i];
-    if (a.fR[f] < 0) continue;
-    const int side = a.cside[(int64_t)(s - 1) * nc + i];
-    double r[20];
-#pragma unroll
-    for (int q = 0; q < 5; ++q) {
-#pragma unroll
-      for (int c4 = 0; c4 < 4; ++c4) {
-        const double* J = a.Jr + (int64_t)(CGKS_RJ_SELF + ((s - 1) * 5 + q) * 40 + 10 * c4) * nc + i;
-        double v = 0.0;
-#pragma unroll
-        for (int j = 0; j < 10; ++j) v += J[(int64_t)j * nc] * cb[10 * q + j];
-        r[c4 == 0 ? q : 5 + 3 * q + (c4 - 1)] = v;
-      }
-    }
-    double2* rec = reinterpret_cast<double2*>(a.rec + (2 * f + side) * 20);
-#pragma unroll
-    for (int k = 0; k < 10; ++k) rec[k] = make_double2(r[2 * k], r[2 * k + 1]);
-  }
+  for (int g = ty; g < 20 + 6 * 5; g += 16) vjp_slot_body(i, g, a, &cbs[0][tx], 32);
 }
 
 __global__ void __launch_bounds__(128) k_vjp_cells(VjpArgs a) {
@@ -342,6 +267,7 @@ static cgks_status adjoint_buffers(cgks_ctx* ctx) {
   CKS(dalloc(ctx, M, &ctx->pbar, (size_t)CGKS_PB * F.ngp));
   CKS(dalloc(ctx, M, &ctx->aself, (size_t)20 * F.nc));
   CKS(dalloc(ctx, M, &ctx->arec, (size_t)20 * 2 * F.nf));
+  CKS(dalloc(ctx, M, &ctx->acb, (size_t)CGKS_RJ_OUT * F.nc));
   // work vectors: mu, v, wbar, g, lambda, F+, F- (20 rows each) and one row of per-cell scalars
   CKS(dalloc(ctx, M, &ctx->avec, (size_t)(7 * 20 + 1) * F.nc));
   return CGKS_OK;
@@ -350,9 +276,10 @@ static cgks_status adjoint_buffers(cgks_ctx* ctx) {
 static cgks_status run_vjp(cgks_ctx* ctx, const double* rbar, const double* gbar, double* out) {
   const Fine& F = ctx->F;
   VjpArgs va{F.nc, F.nf, F.ngp, F.ctype, F.cside, F.cf, F.fL, F.fR, F.gp_face, F.gp_ptr, F.gp_x, F.gp_A, F.fshift,
-             F.ctr, F.vol, ctx->adt, ctx->Jp, ctx->Jr, rbar, gbar, ctx->pbar, ctx->aself, ctx->arec, out};
+             F.ctr, F.vol, ctx->adt, ctx->Jp, ctx->Jr, rbar, gbar, ctx->pbar, ctx->aself, ctx->arec, ctx->acb, out};
   k_vjp_points<<<grid_for(F.ngp, 128), 128, 0, ctx->stream>>>(va);
-  k_vjp_recon<<<grid_for(F.nc, 128), 128, 0, ctx->stream>>>(va);
+  k_vjp_coef<<<grid_for(F.nc, 128), 128, 0, ctx->stream>>>(va);
+  k_vjp_slots<<<grid_for(F.nc, 32), dim3(32, 16), 0, ctx->stream>>>(va);
   k_vjp_cells<<<grid_for(F.nc, 128), 128, 0, ctx->stream>>>(va);
   CK(cudaGetLastError());
   return CGKS_OK;

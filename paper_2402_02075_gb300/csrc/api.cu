@@ -342,7 +342,7 @@ cgks_status cgks_mesh_upload(cgks_ctx* ctx, int64_t n_nodes, const double* xyz, 
   free_list(ctx->mesh_allocs);
   // the adjoint's arrays were in mesh_allocs
   ctx->Jp = ctx->Jr = ctx->adt = ctx->pbar = ctx->aself = ctx->arec = ctx->avec = ctx->apart = ctx->akry = nullptr;
-  ctx->ajc = nullptr;
+  ctx->ajc = ctx->acb = nullptr;
   ctx->F = Fine();
   ctx->L.clear();
   ctx->C.clear();

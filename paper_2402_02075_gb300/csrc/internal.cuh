@@ -111,6 +111,7 @@ struct cgks_ctx {
   double *Jp = nullptr, *Jr = nullptr, *adt = nullptr;
   double *pbar = nullptr, *aself = nullptr, *arec = nullptr, *avec = nullptr, *apart = nullptr, *akry = nullptr;
   double* ajc = nullptr;  // per-cell shares of the wall force
+  double* acb = nullptr;  // per-cell coefficient cotangents of a transposed product
   bool linearized = false;
   // host copy of the uploaded mesh (shape derivatives re-upload it with displaced nodes)
   std::vector<double> h_xyz;
