@@ -1,0 +1,141 @@
+"""The library's gas-kinetic point flux, compiled for the host, against the oracle's independent
+point flux; and its forward-mode linearisation (the code the adjoint stores) against central
+differences of the oracle.  The kernel bodies are host+device functions, so this runs without a
+GPU: it checks the CUDA path's arithmetic, not the device.  Tolerances as in the GPU parity tests
+(1e-11 of the terms' scale for values; 1e-8 for derivatives against Richardson-extrapolated
+differences)."""
+import ctypes as C
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2402_02075_gb300", "csrc")
+
+HARNESS = r'''
+#include "fine.cuh"
+
+static Phys phys(const double* p) {
+  Phys ph{};
+  ph.gamma = p[0];
+  ph.K = (5.0 - 3.0 * p[0]) / (p[0] - 1.0);
+  ph.mu = p[1];
+  ph.prandtl = p[2];
+  ph.eps_inviscid = p[3];
+  ph.c_press = p[4];
+  ph.viscous = p[1] > 0.0;
+  ph.cf = 0;
+  return ph;
+}
+
+extern "C" int host_point_flux(const double* p, const double* WL, const double* GL, const double* WR, const double* GR,
+                               const double* n, double dt, double* F, double* Wt) {
+  const Phys ph = phys(p);
+  DevErr err{};
+  double al;
+  point_flux<double>(n, 1.0, false, 0, WL, GL, WR, GR, dt, ph, F, Wt, al, &err, 0);
+  return err.code;
+}
+
+extern "C" int host_point_jvp(const double* p, const double* WL, const double* GL, const double* WR, const double* GR,
+                              const double* n, double dt, const double* d, double* dF, double* dWt) {
+  const Phys ph = phys(p);
+  DevErr err{};
+  DualD wl[5], gl[15], wr[5], gr[15], F[5], Wt[5], al;
+  for (int q = 0; q < 5; ++q) {
+    wl[q] = DualD(WL[q], d[q]);
+    wr[q] = DualD(WR[q], d[20 + q]);
+  }
+  for (int j = 0; j < 15; ++j) {
+    gl[j] = DualD(GL[j], d[5 + j]);
+    gr[j] = DualD(GR[j], d[25 + j]);
+  }
+  point_flux<DualD>(n, 1.0, false, 0, wl, gl, wr, gr, DualD(dt, d[40]), ph, F, Wt, al, &err, 0);
+  for (int q = 0; q < 5; ++q) {
+    dF[q] = F[q].d;
+    dWt[q] = Wt[q].d;
+  }
+  return err.code;
+}
+'''
+
+
+@pytest.fixture(scope="module")
+def host(tmp_path_factory):
+    nvcc = shutil.which("nvcc") or ("/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else None)
+    if nvcc is None:
+        pytest.skip("nvcc not available")
+    d = tmp_path_factory.mktemp("host_bodies")
+    src, lib = d / "harness.cu", d / "harness.so"
+    src.write_text(HARNESS)
+    subprocess.run([nvcc, "-std=c++17", "-O2", "-Xcompiler", "-fPIC", "-shared", "--expt-relaxed-constexpr",
+                    "-I" + os.path.join(ROOT, "include"), "-I" + CSRC, "-o", str(lib), str(src)], check=True)
+    L = C.CDLL(str(lib))
+    d_ = C.c_void_p
+    L.host_point_flux.argtypes = [d_] * 6 + [C.c_double, d_, d_]
+    L.host_point_jvp.argtypes = [d_] * 6 + [C.c_double, d_, d_, d_]
+    return L
+
+
+def _p(a):
+    return np.ascontiguousarray(a, dtype=np.float64).ctypes.data_as(C.c_void_p)
+
+
+def _cases(rng, n_cases=6):
+    def state():
+        rho, u, p = 0.8 + 0.4 * rng.random(), rng.normal(size=3) * 0.5, 0.6 + 0.3 * rng.random()
+        return np.array([rho, *(rho * u), p / 0.4 + 0.5 * rho * u @ u])
+    for _ in range(n_cases):
+        n = rng.normal(size=3)
+        yield state(), rng.normal(size=15) * 0.2, state(), rng.normal(size=15) * 0.2, n / np.linalg.norm(n)
+
+
+PHYS = [dict(mach=0.5), dict(mach=0.5, viscous=1, reynolds=500.0, prandtl=0.72),
+        dict(mach=0.5, viscous=1, reynolds=500.0, prandtl=1.0)]
+
+
+def _host_params(prm):
+    mu = prm.get("mach", 0.2) / prm["reynolds"] if prm.get("viscous") else 0.0
+    return np.array([1.4, mu, prm.get("prandtl", 1.0), 0.01, 1.0])
+
+
+@pytest.mark.parametrize("prm", PHYS)
+def test_point_flux_body_matches_the_oracle(orc, host, prm):
+    op, hp = orc.params(**prm), _host_params(prm)
+    rng = np.random.default_rng(31)
+    dt = 0.01
+    for WL, GL, WR, GR, n in _cases(rng):
+        F, Wt = np.zeros(5), np.zeros(5)
+        assert host.host_point_flux(_p(hp), _p(WL), _p(GL), _p(WR), _p(GR), _p(n), dt, _p(F), _p(Wt)) == 0
+        Fo, Wto = orc.gks_point(op, WL, GL, WR, GR, n, dt)
+        assert np.abs(F - Fo).max() <= 1e-11 * np.abs(Fo).max(), (F, Fo)
+        assert np.abs(Wt - Wto).max() <= 1e-11 * np.abs(Wto).max(), (Wt, Wto)
+
+
+@pytest.mark.parametrize("prm", PHYS)
+def test_point_linearisation_matches_oracle_differences(orc, host, prm):
+    """The directional derivative that the adjoint's stored Jacobian holds, against Richardson-
+    extrapolated central differences of the oracle's point flux in the same direction (inputs: both
+    sides' states and gradients and the time step)."""
+    op, hp = orc.params(**prm), _host_params(prm)
+    rng = np.random.default_rng(32)
+    dt = 0.01
+    for WL, GL, WR, GR, n in _cases(rng, 4):
+        x = np.concatenate([WL, GL, WR, GR, [dt]])
+        d = rng.normal(size=41) * np.concatenate([np.abs(WL), np.full(15, 0.2), np.abs(WR), np.full(15, 0.2), [dt]])
+        dF, dWt = np.zeros(5), np.zeros(5)
+        assert host.host_point_jvp(_p(hp), _p(WL), _p(GL), _p(WR), _p(GR), _p(n), dt, _p(d), _p(dF), _p(dWt)) == 0
+
+        def f(y):
+            F, Wt = orc.gks_point(op, y[:5], y[5:20], y[20:25], y[25:40], n, y[40])
+            return np.concatenate([F, Wt])
+
+        def cd(h):
+            return (f(x + h * d) - f(x - h * d)) / (2 * h)
+
+        ref = (4.0 * cd(0.5e-6) - cd(1e-6)) / 3.0
+        got = np.concatenate([dF, dWt])
+        assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max(), (got, ref)
