@@ -40,6 +40,28 @@ extern "C" int host_point_flux(const double* p, const double* WL, const double* 
   return err.code;
 }
 
+extern "C" void host_kfvs(double gamma, const double* WL, const double* WR, const double* n, double* F) {
+  kfvs_flux<double>(WL, WR, n, (5.0 - 3.0 * gamma) / (gamma - 1.0), gamma - 1.0, F);
+}
+
+extern "C" int host_ghost(int tag, double gamma, const double* Winf, const double* n, const double* W, const double* G,
+                          double* Wg, double* Gg) {
+  return bc_ghost<double>(tag, n, W, G, Wg, Gg, gamma, Winf) ? 0 : 1;
+}
+
+extern "C" void host_kfvs_jvp32(double gamma, const double* WL, const double* WR, const double* dL, const double* dR,
+                                const double* n, double* dF) {
+  Dual<float> wl[5], wr[5], nn[3], F[5];
+  for (int q = 0; q < 5; ++q) {
+    wl[q] = Dual<float>((float)WL[q], (float)dL[q]);
+    wr[q] = Dual<float>((float)WR[q], (float)dR[q]);
+  }
+  for (int d = 0; d < 3; ++d) nn[d] = Dual<float>((float)n[d], 0.0f);
+  const float K = (float)((5.0 - 3.0 * gamma) / (gamma - 1.0));
+  kfvs_flux<Dual<float>>(wl, wr, nn, Dual<float>(K, 0.0f), Dual<float>((float)(gamma - 1.0), 0.0f), F);
+  for (int q = 0; q < 5; ++q) dF[q] = F[q].d;
+}
+
 extern "C" int host_point_jvp(const double* p, const double* WL, const double* GL, const double* WR, const double* GR,
                               const double* n, double dt, const double* d, double* dF, double* dWt) {
   const Phys ph = phys(p);
@@ -77,6 +99,9 @@ def host(tmp_path_factory):
     d_ = C.c_void_p
     L.host_point_flux.argtypes = [d_] * 6 + [C.c_double, d_, d_]
     L.host_point_jvp.argtypes = [d_] * 6 + [C.c_double, d_, d_, d_]
+    L.host_kfvs.argtypes = [C.c_double, d_, d_, d_, d_]
+    L.host_ghost.argtypes = [C.c_int, C.c_double] + [d_] * 6
+    L.host_kfvs_jvp32.argtypes = [C.c_double] + [d_] * 6
     return L
 
 
@@ -139,3 +164,46 @@ def test_point_linearisation_matches_oracle_differences(orc, host, prm):
         ref = (4.0 * cd(0.5e-6) - cd(1e-6)) / 3.0
         got = np.concatenate([dF, dWt])
         assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max(), (got, ref)
+
+
+def test_kfvs_body_matches_the_oracle(orc, host):
+    """The coarse-level first-order flux (KFVS) of the CUDA path against the oracle's."""
+    op = orc.params()
+    rng = np.random.default_rng(33)
+    for WL, _, WR, _, n in _cases(rng, 8):
+        F = np.zeros(5)
+        host.host_kfvs(1.4, _p(WL), _p(WR), _p(n), _p(F))
+        Fo = orc.kfvs_point(op, WL, WR, n)
+        assert np.abs(F - Fo).max() <= 1e-13 * np.abs(Fo).max(), (F, Fo)
+
+
+@pytest.mark.parametrize("tag", [1, 2, 3, 4, 5])
+def test_ghost_states_match_the_oracle(orc, host, tag):
+    """Ghost states and gradients of the five boundary kinds (slip wall, no-slip wall, farfield by
+    Riemann invariants, supersonic inflow, supersonic outflow), subsonic and supersonic normal
+    velocities, against the oracle's."""
+    for mach in (0.5, 3.0):
+        op = orc.params(mach=mach)
+        u = np.array([mach, 0.0, 0.0])
+        Winf = np.array([1.0, *u, 1.0 / 1.4 / 0.4 + 0.5 * u @ u])
+        rng = np.random.default_rng(34 + tag)
+        for WL, GL, _, _, n in _cases(rng, 6):
+            Wg, Gg = np.zeros(5), np.zeros(15)
+            assert host.host_ghost(tag, 1.4, _p(Winf), _p(n), _p(WL), _p(GL), _p(Wg), _p(Gg)) == 0
+            Wo, Go = orc.bc_ghost(op, tag, n, WL, GL)
+            assert np.abs(Wg - Wo).max() <= 1e-13 * np.abs(Wo).max(), (tag, Wg, Wo)
+            assert np.abs(Gg - Go).max() <= 1e-13 * max(np.abs(Go).max(), 1e-300) or np.abs(Gg - Go).max() == 0.0, (tag, Gg, Go)
+
+
+def test_fp32_kfvs_linearisation_matches_oracle_differences(orc, host):
+    """The FP32 forward-mode KFVS derivative of the mixed-precision coarse levels against central
+    differences of the oracle's FP64 KFVS flux: FP32 accuracy (1e-5 of the derivative's scale)."""
+    op = orc.params()
+    rng = np.random.default_rng(35)
+    for WL, _, WR, _, n in _cases(rng, 8):
+        dL, dR = rng.normal(size=5) * np.abs(WL) * 1e-2, rng.normal(size=5) * np.abs(WR) * 1e-2
+        dF = np.zeros(5)
+        host.host_kfvs_jvp32(1.4, _p(WL), _p(WR), _p(dL), _p(dR), _p(n), _p(dF))
+        h = 1e-4
+        ref = (orc.kfvs_point(op, WL + h * dL, WR + h * dR, n) - orc.kfvs_point(op, WL - h * dL, WR - h * dR, n)) / (2 * h)
+        assert np.abs(dF - ref).max() <= 1e-5 * np.abs(ref).max(), (dF, ref)
