@@ -16,7 +16,10 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_2402_02075_gb300", "csrc")
 
 HARNESS = r'''
+#include <vector>
+
 #include "fine.cuh"
+#include "recon_ops.cuh"
 
 static Phys phys(const double* p) {
   Phys ph{};
@@ -62,6 +65,34 @@ extern "C" void host_kfvs_jvp32(double gamma, const double* WL, const double* WR
   for (int q = 0; q < 5; ++q) dF[q] = F[q].d;
 }
 
+// the reconstruction operators of every cell from its geometry, then the WENO reconstruction and the
+// local time step of every cell; p = (gamma, mu, prandtl, weno_eps, cfl, Winf[5])
+extern "C" int host_reconstruct(int64_t nc, int64_t nf, const int8_t* ctype, const int32_t* cf, const int8_t* cside,
+                                const int32_t* fL, const int32_t* fR, const int32_t* ftag, const double* vol,
+                                const double* ctr, const double* m2, const double* Sn, const double* area,
+                                const double* fshift, const double* fctr, const double* fnrm, const double* W,
+                                const double* G, const double* alpha, const double* p, double* rc, double* dt) {
+  std::vector<double> Kop(216 * nc), ggw(18 * nc), lsw(18 * nc), aux(8 * nc), dtw(24 * nc);
+  DevErr err{};
+  ROArgs ro{nc, nf, ctype, cf, cside, fL, fR, vol, ctr, m2, Sn, area, fshift, fctr, fnrm,
+            Kop.data(), ggw.data(), lsw.data(), aux.data(), dtw.data(), &err};
+  for (int64_t i = 0; i < nc; ++i) recon_ops_body(i, ro);
+  if (err.code) return 100 + err.code;
+  Phys ph{};
+  ph.gamma = p[0];
+  ph.K = (5.0 - 3.0 * p[0]) / (p[0] - 1.0);
+  ph.mu = p[1];
+  ph.prandtl = p[2];
+  ph.weno_eps = p[3];
+  ph.cfl_fine = p[4];
+  ph.viscous = p[1] > 0.0;
+  for (int q = 0; q < 5; ++q) ph.Winf[q] = p[5 + q];
+  ReconArgs ra{nc, nf, ctype, cf, fL, fR, ftag, cside, fnrm, Kop.data(), ggw.data(), lsw.data(), aux.data(),
+               dtw.data(), vol, W, G, alpha, rc, dt, ph, &err};
+  for (int64_t i = 0; i < nc; ++i) reconstruct_body(i, ra);
+  return err.code;
+}
+
 extern "C" int host_point_jvp(const double* p, const double* WL, const double* GL, const double* WR, const double* GR,
                               const double* n, double dt, const double* d, double* dF, double* dWt) {
   const Phys ph = phys(p);
@@ -102,6 +133,7 @@ def host(tmp_path_factory):
     L.host_kfvs.argtypes = [C.c_double, d_, d_, d_, d_]
     L.host_ghost.argtypes = [C.c_int, C.c_double] + [d_] * 6
     L.host_kfvs_jvp32.argtypes = [C.c_double] + [d_] * 6
+    L.host_reconstruct.argtypes = [C.c_int64, C.c_int64] + [d_] * 20
     return L
 
 
@@ -207,3 +239,69 @@ def test_fp32_kfvs_linearisation_matches_oracle_differences(orc, host):
         h = 1e-4
         ref = (orc.kfvs_point(op, WL + h * dL, WR + h * dR, n) - orc.kfvs_point(op, WL - h * dL, WR - h * dR, n)) / (2 * h)
         assert np.abs(dF - ref).max() <= 1e-5 * np.abs(ref).max(), (dF, ref)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32).ctypes.data_as(C.c_void_p)
+
+
+def _i8(a):
+    return np.ascontiguousarray(a, dtype=np.int8).ctypes.data_as(C.c_void_p)
+
+
+RECON_CASES = {
+    "mixed periodic": (lambda mg: mg.periodic_box(6), dict(mach=0.5)),
+    "wall box": (lambda mg: mg.wall_box(8, 4, 8, n_prism=3), dict(mach=0.5, viscous=1, reynolds=1e3, prandtl=0.72)),
+    "ramp": (lambda mg: mg.ramp_box(8, 4, 2, n_prism=1), dict(mach=3.0)),
+    "pyramids": (lambda mg: mg.pyramid_box(6, periodic=False), dict(mach=0.5)),
+}
+
+
+@pytest.mark.parametrize("name", list(RECON_CASES))
+def test_reconstruction_body_matches_the_oracle(orc, host, name):
+    """The CUDA path's reconstruction-operator precompute and WENO reconstruction (Sec. 3), run on the
+    host from the oracle's cell and face geometry, against the oracle's reconstruction (which solves
+    the constrained least-squares problem per call) and its local time steps."""
+    import meshgen as mg
+    mk, prm = RECON_CASES[name]
+    mesh = mk(mg)
+    om = orc.Mesh(mesh)
+    nc, nf = om.nc, om.nf
+    vol, ctr, m2 = om.cells()
+    F = om.faces()
+    ngp = F["ngp"]
+    mask = (np.arange(4)[None, :] < ngp[:, None])[:, :, None]
+    gA, gx = np.where(mask, F["gA"], 0.0), np.where(mask, F["gx"], 0.0)
+    Sn = gA.sum(1)
+    w = np.linalg.norm(gA, axis=2)
+    area = w.sum(1)
+    fctr = (w[:, :, None] * gx).sum(1) / area[:, None]
+    fnrm = Sn / np.linalg.norm(Sn, axis=1)[:, None]
+    rng = np.random.default_rng(41)
+    mach = prm["mach"]
+    W, G = mg.uniform_state(nc, mach=mach)
+    amp = 0.003 if mach > 1 else 0.02
+    W = W * (1.0 + amp * rng.standard_normal(W.shape))
+    G = 2.5 * amp * rng.standard_normal(G.shape)
+    alpha = 1.0 - 0.1 * rng.random(nc)
+    op = orc.params(n_levels=1, **prm)
+    u = np.array([mach, 0.0, 0.0])
+    p = np.array([1.4, mach / prm["reynolds"] if prm.get("viscous") else 0.0, prm.get("prandtl", 1.0), 1e-5, 0.5,
+                  1.0, *u, 1.0 / 1.4 / 0.4 + 0.5 * u @ u])
+    rc = np.zeros((nc, 50))
+    dt = np.zeros(nc)
+    T = np.ascontiguousarray
+    code = host.host_reconstruct(nc, nf, _i8(mesh["cell_type"]), _i32(F["cf"].T), _i8(F["cside"].T), _i32(F["fL"]),
+                                 _i32(F["fR"]), _i32(F["tag"]), _p(vol), _p(T(ctr.T)), _p(T(m2.T)), _p(T(Sn.T)),
+                                 _p(area), _p(T(F["shift"].T)), _p(T(fctr.T)), _p(T(fnrm.T)), _p(W), _p(G), _p(alpha),
+                                 _p(p), _p(rc), _p(dt))
+    assert code == 0
+    os_ = orc.Solver(om, op)
+    os_.set_state(W, G, alpha)
+    ref = os_.reconstruct(0).reshape(nc, 50)
+    for q in range(5):
+        blk, rblk = rc[:, 10 * q:10 * q + 10], ref[:, 10 * q:10 * q + 10]
+        err = np.linalg.norm(blk - rblk) / np.linalg.norm(rblk)
+        assert err <= 1e-10, (name, q, err)
+    dto = os_.residual()["dt"]
+    assert np.abs(dt - dto).max() <= 1e-13 * np.abs(dto).max()
