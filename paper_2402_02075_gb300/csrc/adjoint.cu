@@ -45,29 +45,7 @@ __global__ void __launch_bounds__(128) k_recon_jac(ReconArgs a, double* Jr) {
 
 __global__ void __launch_bounds__(128) k_vjp_points(VjpArgs a) {
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (g >= a.ngp) return;
-  const int64_t ngp = a.ngp, nc = a.nc;
-  const int64_t f = a.gp_face[g], L = a.fL[f], R = a.fR[f];
-  const double A[3] = {a.gp_A[g], a.gp_A[ngp + g], a.gp_A[2 * ngp + g]};
-  // the left cell takes -flux and +A x state / |Omega|; the right cell the opposite
-  double ub[10];
-  const double rvL = 1.0 / a.vol[L], rvR = R >= 0 ? 1.0 / a.vol[R] : 0.0;
-#pragma unroll
-  for (int q = 0; q < 5; ++q) {
-    ub[q] = -a.rbar[q * nc + L] + (R >= 0 ? a.rbar[q * nc + R] : 0.0);
-    double s = 0.0;
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-      s += A[d] * (a.gbar[(3 * q + d) * nc + L] * rvL - (R >= 0 ? a.gbar[(3 * q + d) * nc + R] * rvR : 0.0));
-    ub[5 + q] = s;
-  }
-  for (int k = 0; k < CGKS_PJ_IN; ++k) {
-    const double* J = a.Jp + (int64_t)(CGKS_PJ_OUT * k) * ngp + g;
-    double s = 0.0;
-#pragma unroll
-    for (int o = 0; o < CGKS_PJ_OUT; ++o) s += J[(int64_t)o * ngp] * ub[o];
-    a.pbar[(int64_t)g * CGKS_PB + k] = s;
-  }
+  if (g < a.ngp) vjp_point_body(g, a);
 }
 
 __global__ void __launch_bounds__(128) k_vjp_coef(VjpArgs a) {
@@ -89,26 +67,7 @@ __global__ void __launch_bounds__(512) k_vjp_slots(VjpArgs a) {
 
 __global__ void __launch_bounds__(128) k_vjp_cells(VjpArgs a) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= a.nc) return;
-  const int64_t nc = a.nc;
-  const int nt = a.ctype[i] == 7 ? 5 : a.ctype[i];
-  double v[20];
-#pragma unroll
-  for (int c = 0; c < 20; ++c) v[c] = a.self[(int64_t)c * nc + i];
-  for (int m = 0; m < nt; ++m) {
-    const int64_t f = a.cf[(int64_t)m * nc + i];
-    if (a.fR[f] < 0) continue;
-    const int other = 1 - a.cside[(int64_t)m * nc + i];
-    const double2* rec = reinterpret_cast<const double2*>(a.rec + (2 * f + other) * 20);
-#pragma unroll
-    for (int k = 0; k < 10; ++k) {
-      const double2 r = rec[k];
-      v[2 * k] += r.x;
-      v[2 * k + 1] += r.y;
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < 20; ++c) a.out[(int64_t)c * nc + i] = v[c];
+  if (i < a.nc) vjp_cell_body(i, a);
 }
 
 // ---- functional, adjoint iteration, reductions ---------------------------------------------------

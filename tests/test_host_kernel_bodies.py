@@ -18,7 +18,7 @@ CSRC = os.path.join(ROOT, "paper_2402_02075_gb300", "csrc")
 HARNESS = r'''
 #include <vector>
 
-#include "fine.cuh"
+#include "adjoint.cuh"
 #include "recon_ops.cuh"
 
 static Phys phys(const double* p) {
@@ -93,6 +93,61 @@ extern "C" int host_reconstruct(int64_t nc, int64_t nf, const int8_t* ctype, con
   return err.code;
 }
 
+// the whole fine residual (Res, Gnew, alpha) of the CUDA path on the host, and, when rbar != NULL,
+// the adjoint's transposed product (stored Jacobians and the four transposed-product bodies)
+extern "C" int host_fine(int64_t nc, int64_t nf, int64_t ngp, const int8_t* ctype, const int32_t* cf,
+                         const int8_t* cside, const int32_t* fL, const int32_t* fR, const int32_t* ftag,
+                         const int32_t* gp_ptr, const int32_t* gp_face, const double* gp_x, const double* gp_A,
+                         const double* vol, const double* ctr, const double* m2, const double* Sn, const double* area,
+                         const double* fshift, const double* fctr, const double* fnrm, const double* W, const double* G,
+                         const double* alpha, const double* p, int cf_on, double* res, double* Gout, double* aout,
+                         const double* rbar, const double* gbar, double* out) {
+  std::vector<double> Kop(216 * nc), ggw(18 * nc), lsw(18 * nc), aux(8 * nc), dtw(24 * nc);
+  DevErr err{};
+  ROArgs ro{nc, nf, ctype, cf, cside, fL, fR, vol, ctr, m2, Sn, area, fshift, fctr, fnrm,
+            Kop.data(), ggw.data(), lsw.data(), aux.data(), dtw.data(), &err};
+  for (int64_t i = 0; i < nc; ++i) recon_ops_body(i, ro);
+  if (err.code) return 100 + err.code;
+  Phys ph{};
+  ph.gamma = p[0];
+  ph.K = (5.0 - 3.0 * p[0]) / (p[0] - 1.0);
+  ph.mu = p[1];
+  ph.prandtl = p[2];
+  ph.weno_eps = p[3];
+  ph.cfl_fine = p[4];
+  ph.eps_inviscid = 0.01;
+  ph.c_press = 1.0;
+  ph.viscous = p[1] > 0.0;
+  ph.cf = cf_on;
+  for (int q = 0; q < 5; ++q) ph.Winf[q] = p[5 + q];
+  std::vector<double> rc(50 * nc + 2), dt(nc), gpF(5 * ngp), gpW(5 * ngp), gpa(ngp);
+  double* rca = rc.data() + ((reinterpret_cast<uintptr_t>(rc.data()) & 15) ? 1 : 0);  // 16-byte aligned
+  ReconArgs ra{nc, nf, ctype, cf, fL, fR, ftag, cside, fnrm, Kop.data(), ggw.data(), lsw.data(), aux.data(),
+               dtw.data(), vol, W, G, alpha, rca, dt.data(), ph, &err};
+  for (int64_t i = 0; i < nc; ++i) reconstruct_body(i, ra);
+  PointArgs pa{ngp, nf, nc, gp_face, fL, fR, ftag, gp_x, gp_A, fshift, ctr, rca, dt.data(), gpF.data(), gpW.data(),
+               gpa.data(), ph, &err};
+  for (int64_t g = 0; g < ngp; ++g) gks_point_body(g, pa);
+  GatherArgs ga{nc, ngp, ctype, cside, cf, gp_ptr, gp_A, gpF.data(), gpW.data(), gpa.data(), vol, dt.data(), W,
+                nullptr, res, Gout, aout, 0, ph.gamma, &err};
+  for (int64_t i = 0; i < nc; ++i) gather_body(i, ga);
+  if (err.code || !rbar) return err.code;
+  std::vector<double> Jr((size_t)CGKS_RJ_ROWS * nc), Jp((size_t)CGKS_PJ_IN * CGKS_PJ_OUT * ngp);
+  for (int64_t i = 0; i < nc; ++i) recon_jacobian_body(i, ra, Jr.data());
+  for (int64_t g = 0; g < ngp; ++g) point_jacobian_body(g, pa, Jp.data());
+  std::vector<double> pbar(CGKS_PB * ngp + 2), self(20 * nc), rec(40 * nf + 2), cbuf(CGKS_RJ_OUT * nc);
+  double* pb = pbar.data() + ((reinterpret_cast<uintptr_t>(pbar.data()) & 15) ? 1 : 0);
+  double* rr = rec.data() + ((reinterpret_cast<uintptr_t>(rec.data()) & 15) ? 1 : 0);
+  VjpArgs va{nc, nf, ngp, ctype, cside, cf, fL, fR, gp_face, gp_ptr, gp_x, gp_A, fshift, ctr, vol, dt.data(),
+             Jp.data(), Jr.data(), rbar, gbar, pb, self.data(), rr, cbuf.data(), out};
+  for (int64_t g = 0; g < ngp; ++g) vjp_point_body(g, va);
+  for (int64_t i = 0; i < nc; ++i) vjp_coef_body(i, va);
+  for (int64_t i = 0; i < nc; ++i)
+    for (int k = 0; k < 50; ++k) vjp_slot_body(i, k, va, cbuf.data() + i, (int)nc);
+  for (int64_t i = 0; i < nc; ++i) vjp_cell_body(i, va);
+  return err.code;
+}
+
 extern "C" int host_point_jvp(const double* p, const double* WL, const double* GL, const double* WR, const double* GR,
                               const double* n, double dt, const double* d, double* dF, double* dWt) {
   const Phys ph = phys(p);
@@ -134,6 +189,7 @@ def host(tmp_path_factory):
     L.host_ghost.argtypes = [C.c_int, C.c_double] + [d_] * 6
     L.host_kfvs_jvp32.argtypes = [C.c_double] + [d_] * 6
     L.host_reconstruct.argtypes = [C.c_int64, C.c_int64] + [d_] * 20
+    L.host_fine.argtypes = [C.c_int64] * 3 + [d_] * 22 + [C.c_int] + [d_] * 6
     return L
 
 
@@ -305,3 +361,113 @@ def test_reconstruction_body_matches_the_oracle(orc, host, name):
         assert err <= 1e-10, (name, q, err)
     dto = os_.residual()["dt"]
     assert np.abs(dt - dto).max() <= 1e-13 * np.abs(dto).max()
+
+
+def _fine_inputs(orc, mesh):
+    om = orc.Mesh(mesh)
+    nc, nf = om.nc, om.nf
+    vol, ctr, m2 = om.cells()
+    F = om.faces()
+    ngpf = F["ngp"]
+    mask = (np.arange(4)[None, :] < ngpf[:, None])[:, :, None]
+    gA, gx = np.where(mask, F["gA"], 0.0), np.where(mask, F["gx"], 0.0)
+    Sn = gA.sum(1)
+    w = np.linalg.norm(gA, axis=2)
+    area = w.sum(1)
+    fctr = (w[:, :, None] * gx).sum(1) / area[:, None]
+    fnrm = Sn / np.linalg.norm(Sn, axis=1)[:, None]
+    gp_ptr = np.concatenate([[0], np.cumsum(ngpf)]).astype(np.int32)
+    sel = mask[:, :, 0].ravel()
+    gp_x = np.ascontiguousarray(gx.reshape(-1, 3)[sel].T)
+    gp_A = np.ascontiguousarray(gA.reshape(-1, 3)[sel].T)
+    gp_face = np.repeat(np.arange(nf, dtype=np.int32), ngpf)
+    T = np.ascontiguousarray
+    arrays = [_i8(mesh["cell_type"]), _i32(F["cf"].T), _i8(F["cside"].T), _i32(F["fL"]), _i32(F["fR"]), _i32(F["tag"]),
+              _i32(gp_ptr), _i32(gp_face), _p(gp_x), _p(gp_A), _p(vol), _p(T(ctr.T)), _p(T(m2.T)), _p(T(Sn.T)),
+              _p(area), _p(T(F["shift"].T)), _p(T(fctr.T)), _p(T(fnrm.T))]
+    keep = (gp_ptr, gp_face, gp_x, gp_A, vol, ctr, m2, Sn, area, fctr, fnrm, F)  # alive while the arrays are used
+    return om, nc, nf, int(gp_ptr[-1]), arrays, keep
+
+
+def _phys_vector(prm):
+    mach = prm["mach"]
+    u = np.array([mach, 0.0, 0.0])
+    return np.array([1.4, mach / prm["reynolds"] if prm.get("viscous") else 0.0, prm.get("prandtl", 1.0), 1e-5, 0.5,
+                     1.0, *u, 1.0 / 1.4 / 0.4 + 0.5 * u @ u])
+
+
+FINE_CASES = {
+    "mixed periodic": (lambda mg: mg.periodic_box(6), dict(mach=0.5)),
+    "wall box": (lambda mg: mg.wall_box(8, 4, 8, n_prism=3), dict(mach=0.5, viscous=1, reynolds=1e3, prandtl=0.72)),
+    "ramp": (lambda mg: mg.ramp_box(8, 4, 2, n_prism=1), dict(mach=3.0)),
+    "pyramids": (lambda mg: mg.pyramid_box(6, periodic=False), dict(mach=0.5, viscous=1, reynolds=1e3, prandtl=0.72)),
+}
+
+
+def _state(mg, nc, mach, seed):
+    rng = np.random.default_rng(seed)
+    W, G = mg.uniform_state(nc, mach=mach)
+    amp = 0.003 if mach > 1 else 0.02
+    return W * (1.0 + amp * rng.standard_normal(W.shape)), 2.5 * amp * rng.standard_normal(G.shape), rng
+
+
+@pytest.mark.parametrize("cf_on", [1, 0])
+@pytest.mark.parametrize("name", list(FINE_CASES))
+def test_fine_residual_on_the_host_matches_the_oracle(orc, host, name, cf_on):
+    """The whole fine CGKS residual of the CUDA path (operators, reconstruction, point flux, gather),
+    run on the host, against the oracle's residual, Gauss-Green gradients and compression factors,
+    with the tolerances of the GPU parity tests."""
+    import meshgen as mg
+    from parity import assert_normwise, grad_scale
+    mk, prm = FINE_CASES[name]
+    mesh = mk(mg)
+    om, nc, nf, ngp, arrays, keep = _fine_inputs(orc, mesh)
+    W, G, rng = _state(mg, nc, prm["mach"], 43)
+    alpha = 1.0 - 0.1 * rng.random(nc)
+    res, Gout, aout = np.zeros((5, nc)), np.zeros((15, nc)), np.zeros(nc)
+    code = host.host_fine(nc, nf, ngp, *arrays, _p(W), _p(G), _p(alpha), _p(_phys_vector(prm)), cf_on, _p(res),
+                          _p(Gout), _p(aout), None, None, None)
+    assert code == 0
+    os_ = orc.Solver(om, orc.params(n_levels=1, compression_factor=cf_on, **prm))
+    os_.set_state(W, G, alpha)
+    ro = os_.residual()
+    assert_normwise(res, ro["res"], 1e-11, "residual", scale=ro["fscale"])
+    assert_normwise(Gout, ro["grad"], 1e-11, "Gauss-Green gradients", scale=grad_scale(ro["gscale"]))
+    assert_normwise(aout[None], ro["alpha"][None], 1e-11, "compression factor")
+
+
+@pytest.mark.parametrize("name", list(FINE_CASES))
+def test_adjoint_product_on_the_host_matches_oracle_differences(orc, host, name):
+    """The adjoint's whole transposed product (forward-mode Jacobians of the reconstruction and the
+    point flux, then the four transposed-product bodies), run on the host: w . (J v) = (J^T w) . v
+    with J v a Richardson-extrapolated central difference of the oracle's (Res, Gnew)."""
+    import meshgen as mg
+    mk, prm = FINE_CASES[name]
+    mesh = mk(mg)
+    om, nc, nf, ngp, arrays, keep = _fine_inputs(orc, mesh)
+    W, G, rng = _state(mg, nc, prm["mach"], 44)
+    ones = np.ones(nc)
+    os_ = orc.Solver(om, orc.params(n_levels=1, compression_factor=0, **prm))
+
+    def Fo(x):
+        os_.set_state(x[:5 * nc].reshape(5, nc), x[5 * nc:].reshape(15, nc), ones)
+        r = os_.residual()
+        return np.concatenate([r["res"].ravel(), r["grad"].ravel()])
+
+    u = np.concatenate([W.ravel(), G.ravel()])
+    scale = np.concatenate([np.abs(W).ravel(), (np.abs(G) + 0.1).ravel()])
+    for _ in range(2):
+        v = scale * rng.standard_normal(u.size)
+        w = rng.standard_normal(u.size)
+        out = np.zeros((20, nc))
+        res, Gout, aout = np.zeros((5, nc)), np.zeros((15, nc)), np.zeros(nc)
+        code = host.host_fine(nc, nf, ngp, *arrays, _p(W), _p(G), _p(ones), _p(_phys_vector(prm)), 0, _p(res), _p(Gout),
+                              _p(aout), _p(w[:5 * nc]), _p(w[5 * nc:]), _p(out))
+        assert code == 0
+
+        def jv(h):
+            return (Fo(u + h * v) - Fo(u - h * v)) / (2 * h)
+
+        Jv = (4.0 * jv(0.5e-7) - jv(1e-7)) / 3.0
+        lhs, rhs = float(w @ Jv), float(out.ravel() @ v)
+        assert abs(lhs - rhs) <= 1e-6 * float(np.abs(w) @ np.abs(Jv)), (name, lhs, rhs)
