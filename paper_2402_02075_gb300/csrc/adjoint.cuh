@@ -1,5 +1,5 @@
-// Bodies of the adjoint's transposed-product kernels that work per cell (host+device, so that their
-// arithmetic can be exercised without a device); adjoint.cu wraps them in kernels.
+// Bodies of the adjoint's transposed-product kernels, per Gauss point and per cell (host+device, so
+// that their arithmetic can be exercised without a device); adjoint.cu wraps them in kernels.
 #pragma once
 #include "fine.cuh"
 
