@@ -98,8 +98,16 @@ def test_kfvs_levels_free_stream_and_telescoping(orc):
         assert np.all(np.abs(R.sum(axis=1)) < 1e-14 * np.abs(R).sum(axis=1).max())
 
 
-def _wave_error(orc, n, cfl, T=0.1):
-    mesh = mg.box_mesh(n, 4, 4, lambda i, j, k: np.zeros(np.shape(i), int), periodic=(True, True, True))
+def _wave_error(orc, n, cfl, T=0.1, mixed=False):
+    """L1 density error of a travelling density wave rho = 1 + 0.01 sin(2 pi (x - U t)) after time T,
+    on n x 4 x 4 periodic cubes of side 1/n in y and z (hexahedra, or the quadrant layout of
+    hexahedra, both prism orientations and Kuhn tetrahedra with 5 % jitter), global time step."""
+    h = 1.0 / n
+    if mixed:
+        mesh = mg.box_mesh(n, 4, 4, mg.quadrant_split(3 * n // 4, 3), ys=np.arange(5) * h, zs=np.arange(5) * h,
+                           periodic=(True, True, True), jitter=0.05)
+    else:
+        mesh = mg.box_mesh(n, 4, 4, lambda i, j, k: np.zeros(np.shape(i), int), periodic=(True, True, True))
     M = orc.Mesh(mesh)
     pts, w = M.qpoints(4)
     vol = w.sum(1)
@@ -142,6 +150,16 @@ def test_design_order_on_smooth_density_wave(orc):
     e2 = _wave_error(orc, 32, 0.2)
     assert e1 < 2e-5
     assert np.log2(e1 / e2) > 2.2
+
+
+def test_design_order_on_jittered_mixed_elements(orc):
+    """The same wave on the jittered quadrant layout (hexahedra, prisms of both orientations, Kuhn
+    tetrahedra) at CFL 0.05, where the time error is small: over 8, 16 and 32 cells per wavelength
+    the error falls at a rate of at least 2.5 per halving (third order in space)."""
+    e = [_wave_error(orc, n, 0.05, T=0.05, mixed=True) for n in (8, 16, 32)]
+    rates = [np.log2(e[i] / e[i + 1]) for i in range(2)]
+    assert e[0] < 1e-4
+    assert min(rates) >= 2.5, (e, rates)
 
 
 def test_zero_area_coarse_face_carries_no_flux(orc):
