@@ -3,14 +3,16 @@
 
 A step is one 3-level V-cycle (Sec. 4.2 of the paper: a CGKS pre-smoothing step, the defect at the
 new state, KFVS forward-Euler smoothing with FAS forcing on the two agglomerated levels, injection
-correction) on the laminar boundary-layer box: 96 x 64 x 64 grid, wall-normal grading 1e-4 x 1.1
-(capped at 2 dx), 42 wall layers of prisms and Kuhn tetrahedra above (1,327,104 cells), no-slip wall,
-farfield, Mach 0.5, Re 1e4, Pr 0.72, seeded synthetic mesh and free-stream start.  The metric is
-fine cells x V-cycles per second, for the FP64 V-cycle (value) and the mixed-precision one (mixed);
-`converge` reports wall times to a 1e-10 residual drop of single-grid FP64, FP64 V-cycle and mixed
-V-cycle on small cases (--converge-slab adds the 96 x 4 x 64 slab of the workload's layout).
+correction) on the laminar boundary-layer box: 96 x 64 x 69 grid, wall-normal grading 1e-4 x 1.1
+(capped at 2 dx), 42 wall layers of prisms and Kuhn tetrahedra above (1,511,424 cells), no-slip wall,
+Mach 0.5, Re 1e4, Pr 0.72, seeded synthetic mesh and free-stream start.  The metric is fine cells x
+V-cycles per second, for the FP64 V-cycle (value) and the mixed-precision one (mixed), with a
+roofline entry for every kernel of the cycle; `converge` reports wall times to a 1e-10 residual drop
+of single-grid FP64, FP64 V-cycle and mixed V-cycle (compression factor on) on small ramps and
+boundary layers, a ramp that is not launch-bound and the 96 x 4 x 69 slab of the workload's layout,
+with each final state's error against the oracle's own steady state where one is stored.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--converge-slab]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-converge-slab]
 
 Multi-GPU: one process per GPU (torchrun); each rank runs an independent replica (the method is
 not partitioned in this build), the step time is the maximum over ranks and the value counts the
@@ -33,19 +35,27 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Mcell-iters/s; wall time to 1e-10 residual drop: FP64 vs mixed V-cycle"
 UNIT = "Mcell-iters/s"
-WORKLOAD = dict(nx=96, ny=64, nz=64)
+# the x-out side is the extrapolation outflow (boundary kind 5): a Riemann-invariant farfield there cuts
+# through the boundary layer, and measured, admits distinct discrete steady states and holds the
+# V-cycle at a 3e-5 drop with the compression factor on
+WORKLOAD = dict(nx=96, ny=64, nz=69, outflow=5)
 PARAMS = dict(mach=0.5, reynolds=1e4, prandtl=0.72, gamma=1.4, viscous=1, n_levels=3, cfl_fine=0.5,
               cfl_coarse=0.5, agglo_seed=0)
 # bounded sample of the same workload for the CPU oracle: 4 of its 64 periodic columns in y, i.e. the
 # same x-z layout and physics (82,944 cells)
-SAMPLE = dict(nx=96, ny=4, nz=64)
+SAMPLE = dict(nx=96, ny=4, nz=69, outflow=5)
 # FP64 floating-point operations per Gauss point of the gas-kinetic flux kernel (2 per DFMA, 1 per
 # DADD/DMUL), from the ncu instruction counts of a full capture of the kernel on the 48x32x32 box;
 # the kernel's own arithmetic, all of which the method needs
 FLOP_PER_GP = 3422.8
 # DRAM bytes (read + write) per Gauss point of the same kernel from the same capture (None when the
 # kernel has changed since)
-DRAM_BYTES_PER_GP = 160.7
+DRAM_BYTES_PER_GP = None
+# FP64 operations per cell of the reconstruction kernel, from the ncu instruction counts of a full
+# capture on the same box (DFMA 1,236.5, DMUL 542.9, DADD 356.3 per cell)
+FLOP_PER_CELL_RECON = 3372.2
+# kernels bound by the FP64 pipe (the rest are bound by HBM bandwidth): FLOP per unit
+ALU_KERNELS = {"k_gks_points": FLOP_PER_GP, "k_reconstruct": FLOP_PER_CELL_RECON}
 
 
 def workload_name(w):
@@ -53,7 +63,8 @@ def workload_name(w):
     _, npz = mg.wall_layout(w["nx"], w["nz"])
     cells = w["nx"] * w["ny"] * (2 * npz + 6 * (w["nz"] - npz))
     return (f"3-level FP64 V-cycle, laminar boundary-layer box {w['nx']}x{w['ny']}x{w['nz']} "
-            f"({cells:,} cells: {npz} prism layers + Kuhn tetrahedra), M 0.5, Re 1e4, Pr 0.72")
+            f"({cells:,} cells: {npz} prism layers + Kuhn tetrahedra), no-slip wall, farfield inflow and top, "
+            f"extrapolation outflow, M 0.5, Re 1e4, Pr 0.72")
 
 
 def launches_per_vcycle(P, history=False):
@@ -153,26 +164,89 @@ def job_rate(cells_per_replica, steps, ms_max, world):
     return world * cells_per_replica * steps / (ms_max * 1e-3) / 1e6
 
 
-def cpu_baseline(steps_per_sample=6):
-    """The oracle (as it stands) on a bounded sample of the workload: V-cycles per second x cells."""
+def host_cores():
+    """Cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def oracle_sample(sample, cycles):
+    """The oracle (as it stands) on a bounded sample of the workload: fine cells x V-cycles per
+    second after one warm-up cycle, with the threads OpenMP was given (OMP_NUM_THREADS)."""
     import meshgen as mg
     import oracle
     oracle.build()
-    mesh = mg.wall_box(**SAMPLE)
+    mesh = mg.wall_box(**sample)
     M = oracle.Mesh(mesh)
-    prm = oracle.params(**PARAMS)
-    S = oracle.Solver(M, prm)
+    S = oracle.Solver(M, oracle.params(**PARAMS))
     W, G = mg.uniform_state(M.nc, mach=PARAMS["mach"])
     S.set_state(W, G)
     S.run(1, multigrid=True)  # warm-up (first touch of the work arrays)
     t0 = time.perf_counter()
-    S.run(steps_per_sample, multigrid=True)
+    S.run(cycles, multigrid=True)
     dt = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": M.nc * steps_per_sample / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{steps_per_sample} V-cycles of the same layout and physics at "
-                      f"{SAMPLE['nx']}x{SAMPLE['ny']}x{SAMPLE['nz']} ({M.nc:,} cells), after 1 warm-up cycle",
-            "seconds": dt}
+    return {"value": M.nc * cycles / dt / 1e6, "cells": M.nc, "cycles": cycles, "seconds": dt,
+            "threads": int(os.environ.get("OMP_NUM_THREADS", host_cores()))}
+
+
+def cpu_baseline():
+    """The oracle timed on the host cores at one thread and at all cores, each in a child process
+    (OpenMP fixes its thread count at start-up): V-cycles of the workload's layout and physics on
+    bounded samples of 4 (all cores) and 2 (one thread) of its 64 periodic columns in y."""
+    cores = host_cores()
+    runs = {}
+    for key, threads, sample, cycles in (("all_cores", cores, SAMPLE, 6),
+                                         ("one_thread", 1, dict(SAMPLE, ny=2), 2)):
+        env = dict(os.environ, OMP_NUM_THREADS=str(threads))
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample",
+                            json.dumps({"sample": sample, "cycles": cycles})],
+                           env=env, capture_output=True, text=True, timeout=900)
+        if r.returncode:
+            raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+        runs[key] = json.loads(r.stdout.strip().splitlines()[-1])
+    a, o = runs["all_cores"], runs["one_thread"]
+    return {"value": a["value"], "unit": UNIT, "cores": a["threads"], "kind": "oracle",
+            "sample": f"{a['cycles']} V-cycles of the same layout and physics at {SAMPLE['nx']}x{SAMPLE['ny']}x"
+                      f"{SAMPLE['nz']} ({a['cells']:,} cells), after 1 warm-up cycle",
+            "seconds": a["seconds"],
+            "one_thread": {"value": o["value"], "unit": UNIT, "cores": 1,
+                           "sample": f"{o['cycles']} V-cycles at {SAMPLE['nx']}x2x{SAMPLE['nz']} ({o['cells']:,} "
+                                     f"cells), after 1 warm-up cycle", "seconds": o["seconds"]},
+            "parallel_speedup": a["value"] / o["value"]}
+
+
+def measured_hbm_peak():
+    """The measured HBM copy bandwidth of this GPU (GB/s), or None."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f).get("hbm_gbs")
+    except (OSError, ValueError):
+        return None
+
+
+def kernel_rooflines(stats, steps, fp64_peak, hbm_peak):
+    """Per-kernel roofline of the timed region: stats maps a kernel name to (ms, launches, units,
+    algorithmic bytes) summed over the timed V-cycles.  FP64-pipe kernels: achieved TFLOP/s = FLOP
+    per unit x units / time against the measured FMA-chain peak; the rest: algorithmic bytes / time
+    against the measured HBM copy bandwidth."""
+    out = {}
+    for name, (ms, n, units, by) in stats.items():
+        if n == 0 or ms <= 0:
+            continue
+        row = {"launches_per_step": n / steps, "ms_per_launch": ms / n, "ms_per_step": ms / steps,
+               "units_per_launch": units / n}
+        if name in ALU_KERNELS:
+            ach = ALU_KERNELS[name] * units / (ms * 1e-3) / 1e12
+            row.update(bound="alu", unit="TFLOP/s", achieved=ach, peak=fp64_peak,
+                       frac=ach / fp64_peak if fp64_peak else None, flop_per_unit=ALU_KERNELS[name])
+        else:
+            ach = by / (ms * 1e-3) / 1e9
+            row.update(bound="hbm", unit="GB/s", achieved=ach, peak=hbm_peak,
+                       frac=ach / hbm_peak if hbm_peak else None, algorithmic_bytes_per_launch=by / n)
+        out[name] = row
+    return out
 
 
 def _state_diff(Wa, Wb):
@@ -184,29 +258,54 @@ def _state_diff(Wa, Wb):
 
 
 def converge_cases(slab):
-    """Cases driven to a 1e-10 residual drop: (name, mesh factory, physics, max iterations)."""
+    """Cases driven to a 1e-10 residual drop: (name, mesh factory, physics, max iterations, golden)
+    with golden the name of the oracle's stored steady state of the same case (or None)."""
     import meshgen as mg
     vis = dict(mach=0.5, reynolds=1e4, prandtl=0.72, viscous=1)
-    cases = [("Mach 3 compression ramp 48x24x4, 3 prism layers + hexahedra, inviscid",
-              lambda: mg.ramp_box(48, 24, 4, n_prism=3), dict(mach=3.0), 20000),
-             ("boundary layer 24x4x24 (first 1e-3, ratio 1.2), 17 prism layers + Kuhn tetrahedra, M 0.5, Re 1e4",
-              lambda: mg.wall_box(24, 4, 24, first=1e-3, ratio=1.2), vis, 100000)]
+    out = mg.BC_SUPER_OUT
+    cases = [("Mach 3 compression ramp 32x16x2, 2 prism layers + hexahedra, inviscid",
+              lambda: mg.ramp_box(32, 16, 2, n_prism=2), dict(mach=3.0), 20000, "ramp_32x16x2"),
+             ("Mach 3 compression ramp 64x32x8, 4 prism layers + hexahedra, inviscid",
+              lambda: mg.ramp_box(64, 32, 8, n_prism=4), dict(mach=3.0), 20000, "ramp_64x32x8"),
+             ("Mach 3 compression ramp 128x64x16, 8 prism layers + hexahedra, inviscid (not launch-bound)",
+              lambda: mg.ramp_box(128, 64, 16, n_prism=8), dict(mach=3.0), 20000, None),
+             ("boundary layer 12x2x12 (first 2e-3, ratio 1.3), 12 prism layers, extrapolation outflow, M 0.5, Re 1e4",
+              lambda: mg.wall_box(12, 2, 12, first=2e-3, ratio=1.3, outflow=out), vis, 100000, "wall_12x2x12"),
+             ("boundary layer 24x4x24 (first 1e-3, ratio 1.2), 17 prism layers + Kuhn tetrahedra, extrapolation "
+              "outflow, M 0.5, Re 1e4", lambda: mg.wall_box(24, 4, 24, first=1e-3, ratio=1.2, outflow=out), vis, 100000,
+              None)]
     if slab:
-        # the compression factor off: the flow has no shock, and the factor's non-smooth pressure-jump
-        # terms hold the V-cycle at a 3e-5 floor on this mesh
-        cases.append(("the workload's layout on a 96x4x64 slab (4 periodic columns), M 0.5, Re 1e4, "
-                      "compression factor off", lambda: mg.wall_box(96, 4, 64), dict(vis, compression_factor=0), 60000))
+        cases.append(("the workload's layout on a 96x4x69 slab (4 periodic columns), extrapolation outflow, M 0.5, Re 1e4",
+                      lambda: mg.wall_box(96, 4, 69, outflow=out), vis, 60000, None))
     return cases
 
 
-def run_converge(cg, torch, slab):
-    """Wall time (host clock around the library's own steady-solve loop) to a 1e-10 drop of the
-    density residual for single-grid FP64 CGKS, the FP64 V-cycle, the mixed V-cycle and the FP64
-    V-cycle with the LU-SGS coarse smoother (Sec. 4.3)."""
+def _load_golden(name, it):
+    """The oracle's steady state of a converge case for iteration `it` ("sg" or "vc"), written by
+    tests/golden/make_steady_states.py (which runs only the oracle), or None."""
     import numpy as np
+    if name is None:
+        return None
+    sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
+    import make_steady_states as golden
+    p = golden.reference(name, it)
+    return np.load(p) if os.path.exists(p) else None
+
+
+def run_converge(cg, torch, slab, budget_s=1200.0):
+    """Wall time (host clock around the library's own steady-solve loop) to a 1e-10 drop of the
+    density residual for single-grid FP64 CGKS, the FP64 V-cycle, the mixed V-cycle and (small
+    cases) the FP64 V-cycle with the LU-SGS coarse smoother (Sec. 4.3), all with the compression
+    factor of Sec. 3.3 on.  Each final state is compared with the oracle's own steady state where one
+    is stored, and with the other runs.  Cases are skipped once `budget_s` seconds have passed."""
+    import math
     import meshgen as mg
+    t_start = time.perf_counter()
     out = []
-    for name, mk, phys, max_it in converge_cases(slab):
+    for name, mk, phys, max_it, gold in converge_cases(slab):
+        if time.perf_counter() - t_start > budget_s:
+            out.append({"case": name, "skipped": "time budget of the converge section spent"})
+            continue
         mesh = mk()
         row = {"case": name, "cells": len(mesh["cell_type"])}
         states = {}
@@ -222,18 +321,26 @@ def run_converge(cg, torch, slab):
             r = ctx.steady_solve(multigrid=mgrid, drop=1e-10, max_iters=max_it, raise_on_notconv=False)
             states[key] = ctx.state_get()[0].cpu().numpy()
             row[key] = {"iters": r["iters"], "seconds": r["seconds"], "drop": r["drop"], "converged": r["converged"]}
+            ref = _load_golden(gold, "vc" if mgrid else "sg")
+            if ref is not None:
+                row[key]["state_err_vs_oracle"] = _state_diff(states[key], ref["W"])
+                row[key]["oracle_iteration"] = ("V-cycle" if bool(ref["multigrid"]) else "single grid") + \
+                    f", {int(ref['iters'])} iterations, drop {float(ref['drop']):.1e}"
             ctx.close()
         row["state_diff_mixed_vs_fp64_vcycle"] = _state_diff(states["vcycle_mixed"], states["vcycle_fp64"])
-        sg = row["single_grid_fp64"]
-        if not sg["converged"] and sg["drop"] > 0:
-            # the single grid's last decade rate, extended to 1e-10 (labelled as an extrapolation)
-            import math
-            row["single_grid_fp64"]["extrapolated_seconds_to_1e-10"] = (
-                sg["seconds"] * math.log(1e-10) / math.log(sg["drop"]))
         row["state_diff_vcycle_vs_single_grid"] = _state_diff(states["vcycle_fp64"], states["single_grid_fp64"])
+        sg = row["single_grid_fp64"]
+        if not sg["converged"] and 0 < sg["drop"] < 1:
+            # the single grid's mean rate, extended to 1e-10 (labelled as an extrapolation)
+            sg["extrapolated_seconds_to_1e-10"] = sg["seconds"] * math.log(1e-10) / math.log(sg["drop"])
         out.append(row)
-    return {"target_drop": 1e-10, "clock": "host wall time around cgks_steady_solve (checks the drop every 10 "
-            "iterations)", "cases": out}
+    return {"target_drop": 1e-10, "compression_factor": "on (Sec. 3.3)",
+            "clock": "host wall time around cgks_steady_solve (checks the drop every 10 iterations)",
+            "state_err_vs_oracle": "max over variables of |W - W_oracle| / max |W_oracle| (momentum components "
+                                   "share one scale); W_oracle the oracle's own steady state of the same case from "
+                                   "the same free stream (tests/golden), to a 1e-12 drop, by the same iteration "
+                                   "where the steady state is not unique (the boundary layers)",
+            "seconds": time.perf_counter() - t_start, "cases": out}
 
 
 def run_scale(args):
@@ -273,6 +380,45 @@ def run_scale(args):
     print(json.dumps({"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
                       "data": "synthetic (seeded quadrant-layout boxes, free-stream start)", "dtype": "f64",
                       "scale": rows}))
+
+
+RAMP_WORKLOAD = dict(nx=256, ny=128, nz=128, n_prism=8)
+
+
+def run_ramp_throughput(cg, torch, steps, warmup):
+    """The supersonic compression ramp at size: Mach 3 over 15 degrees, 256 x 128 x 128 grid with 8
+    prism layers at the slip wall and hexahedra above (4,456,448 cells), inviscid, compression factor on
+    (Sec. 3.3).  FP64 and mixed-precision V-cycles timed with CUDA events on the library stream after
+    max(warmup, 20) V-cycles from the free stream (by then the shock stands at the corner and the
+    compression factor is active there)."""
+    import meshgen as mg
+    t0 = time.perf_counter()
+    mesh = mg.ramp_box(**RAMP_WORKLOAD)
+    phys = dict(mach=3.0, n_levels=3)
+    ctx = cg.upload_mesh(mesh, cg.default_params(**phys))
+    setup = time.perf_counter() - t0
+    W, G = mg.uniform_state(ctx.nc, mach=3.0)
+    ctx.state_init(torch.from_numpy(W).cuda(), torch.from_numpy(G).cuda())
+    ctx.vcycle(max(warmup, 20), history=False)
+    out = {"workload": f"Mach 3 compression ramp {RAMP_WORKLOAD['nx']}x{RAMP_WORKLOAD['ny']}x{RAMP_WORKLOAD['nz']}, "
+                       f"{RAMP_WORKLOAD['n_prism']} prism layers + hexahedra, inviscid, compression factor on",
+           "cells": ctx.nc, "setup_s": setup, "unit": UNIT}
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for key, prec in (("vcycle_fp64", 0), ("vcycle_mixed", 1)):
+        ctx.set_params(cg.default_params(precision=prec, **phys))
+        ctx.vcycle(2, history=False)
+        torch.cuda.synchronize()
+        ev0.record(ctx.stream)
+        ctx.vcycle(steps, history=False)
+        ev1.record(ctx.stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / steps
+        out[key] = {"ms_per_cycle": ms, "value": ctx.nc / (ms * 1e-3) / 1e6}
+    a = ctx.state_get()[2]
+    out["alpha_min"] = float(a.min())
+    out["cells_alpha_below_0.99"] = int((a < 0.99).sum())
+    ctx.close()
+    return out
 
 
 ADJ_WORKLOAD = dict(nx=160, ny=80, nz=80, n_prism=8)
@@ -347,11 +493,43 @@ def run_adjoint(args):
                    "stored_linearisation_GB": 8 * (410 * ngp + 2220 * nc) / 1e9,
                    "vjp_bytes_GB": by / 1e9, "vjp_GBps": by / (ms * 1e-3) / 1e9, "hbm_peak_GBps": peak,
                    "frac": (by / (ms * 1e-3) / 1e9) / peak if peak else None}
+    # the same products with the reconstruction's part recomputed (adjoint_recompute 1): only the
+    # point-flux linearisation is stored
+    ctx.set_params(cg.default_params(adjoint_recompute=1, **prm))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.linearize()
+    torch.cuda.synchronize()
+    t_lin_r = time.perf_counter() - t0
+    Wb0, Gb0 = ctx.residual_vjp(rb, gb)
+    for _ in range(args.warmup):
+        ctx.residual_vjp(rb, gb)
+    torch.cuda.synchronize()
+    e0.record(ctx.stream)
+    for _ in range(args.steps):
+        ctx.residual_vjp(rb, gb)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    ms_r = e0.elapsed_time(e1) / args.steps
+    out["full"]["recompute"] = {"linearize_s": t_lin_r, "vjp_ms": ms_r,
+                                "stored_linearisation_GB": 8 * 410 * ngp / 1e9,
+                                "what": "reconstruction's transposed product recomputed per cell in every product "
+                                        "(reverse mode), the point-flux linearisation stored"}
     ctx.close()
     del mesh
     torch.cuda.empty_cache()
-    # (2) whole gradient at a steady state
-    w = ADJ_SMALL
+    # (2) whole gradient at a steady state: the 64 x 32 x 8 ramp and the full 160 x 80 x 80 ramp
+    out["gradient"] = []
+    for w in (ADJ_SMALL, ADJ_WORKLOAD):
+        out["gradient"].append(_adjoint_gradient(cg, torch, mg, w, prm))
+    print(json.dumps(out))
+
+
+def _adjoint_gradient(cg, torch, mg, w, prm):
+    """Steady state from the free stream by single-grid steps, then the gradient of the wall force
+    in the Mach number and 64 wall modes (cgks_adjoint: linearisation, transposed pseudo-time solve,
+    parameter partials), each phase timed; dJ/dMach checked against central differences of the
+    converged functional."""
     mesh = mg.ramp_box(w["nx"], w["ny"], w["nz"], n_prism=w["n_prism"])
     ctx = cg.upload_mesh(mesh, cg.default_params(**prm))
     nc = ctx.nc
@@ -369,24 +547,22 @@ def run_adjoint(args):
     ctx.adjoint(1, None, tol=1e-10)
     t_adj_mach = time.perf_counter() - t0
     Ws, Gs, _ = ctx.state_get()
+    ctx.close()
     J = []
-    for s in (1.0, -1.0):
-        c = cg.upload_mesh(mesh, cg.default_params(**dict(prm, mach=3.0 + s * 1e-6)))
+    for sgn in (1.0, -1.0):
+        c = cg.upload_mesh(mesh, cg.default_params(**dict(prm, mach=3.0 + sgn * 1e-6)))
         c.state_init(Ws, Gs, ad)
         _steady(c)
         J.append(c.wall_force(1))
         c.close()
     fd = (J[0] - J[1]) / 2e-6
-    out["gradient"] = {"workload": f"ramp {w['nx']}x{w['ny']}x{w['nz']}, {w['n_prism']} prism layers", "cells": nc,
-                       "primal_steps": steps, "primal_final_norm": res, "primal_s": t_primal,
-                       "adjoint_iters": g["iters"], "adjoint_rel_res": g["rel_res"],
-                       "gradient_64_modes_and_mach_s": t_adj, "gradient_mach_only_s": t_adj_mach,
-                       "adjoint_solver": "transposed pseudo-time iteration",
-                       "dJ_dmach": g["dJ_dmach"], "dJ_dmach_fd": fd,
-                       "dJ_dmach_rel_err": abs(g["dJ_dmach"] - fd) / abs(fd),
-                       "dJ_dmodes_first4": [float(x) for x in g["dJ_dmodes"][:4]]}
-    ctx.close()
-    print(json.dumps(out))
+    return {"workload": f"ramp {w['nx']}x{w['ny']}x{w['nz']}, {w['n_prism']} prism layers", "cells": nc,
+            "primal_steps": steps, "primal_final_norm": res, "primal_s": t_primal,
+            "adjoint_iters": g["iters"], "adjoint_rel_res": g["rel_res"],
+            "gradient_64_modes_and_mach_s": t_adj, "gradient_mach_only_s": t_adj_mach,
+            "adjoint_solver": "transposed pseudo-time iteration", "dJ_dmach": g["dJ_dmach"], "dJ_dmach_fd": fd,
+            "dJ_dmach_rel_err": abs(g["dJ_dmach"] - fd) / abs(fd),
+            "dJ_dmodes_first4": [float(x) for x in g["dJ_dmodes"][:4]]}
 
 
 def mg_gauss_points(mesh):
@@ -418,7 +594,7 @@ def run_reference(args):
     S.run(args.steps, multigrid=True)
     dt = time.perf_counter() - t0
     value = M.nc * args.steps / dt / 1e6
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = int(os.environ.get("OMP_NUM_THREADS", host_cores()))
     sample = (f"each step one V-cycle of the same layout and physics at {SAMPLE['nx']}x{SAMPLE['ny']}x{SAMPLE['nz']} "
               f"({M.nc:,} cells) instead of the full 96x64x64 box")
     print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -437,16 +613,22 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--converge-slab", action="store_true",
-                    help="also drive the 96x4x64 slab of the workload's layout to 1e-10 (several minutes)")
+    ap.add_argument("--no-converge-slab", action="store_true",
+                    help="leave out the 96x4x69 slab of the workload's layout from the converge cases")
     ap.add_argument("--no-converge", action="store_true")
+    ap.add_argument("--no-ramp", action="store_true", help="leave out the 4.46M-cell supersonic ramp throughput")
     ap.add_argument("--size", default="full", choices=["full", "small"],
                     help="small: the same layout at 48x32x32 (profiling captures only)")
     ap.add_argument("--adjoint", action="store_true",
                     help="adjoint measurements (stored linearisation, transposed product, gradient) instead")
     ap.add_argument("--scale", action="store_true",
                     help="scale sweep at 1.0M / 5.0M / 20.0M cells instead of the benchmark line")
+    ap.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.oracle_sample:
+        spec = json.loads(args.oracle_sample)
+        print(json.dumps(oracle_sample(spec["sample"], spec["cycles"])))
+        return
     global WORKLOAD
     if args.scale:
         run_scale(args)
@@ -455,7 +637,7 @@ def main():
         run_adjoint(args)
         return
     if args.size == "small":
-        WORKLOAD = dict(nx=48, ny=32, nz=32)
+        WORKLOAD = dict(nx=48, ny=32, nz=32, outflow=5)
     if args.impl == "reference":
         run_reference(args)
         return
@@ -508,10 +690,9 @@ def main():
         torch.cuda.synchronize()
     barrier()
     ms = ev0.elapsed_time(ev1)
-    k_ms, k_n = ctx.kernel_stats(0)
-    r_ms, r_n = ctx.kernel_stats(1)
-    g_ms, g_n = ctx.kernel_stats(2)
+    stats = {k: ctx.kernel_stats(k) for k in ctx.KERNELS}
     ctx.profile(False)
+    k_ms, k_n = stats["k_gks_points"][:2]
     ms_max = max_over_ranks(ms)
     value = job_rate(nc, args.steps, ms_max, world)
     # end to end through the public API with host buffers: per step, the state is copied in from
@@ -534,12 +715,15 @@ def main():
     ctx.vcycle(args.warmup, history=False)
     barrier()
     torch.cuda.synchronize()
+    ctx.profile(True)
     ev0.record(stream)
     ctx.vcycle(args.steps, history=False)
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
     ms_mixed = max_over_ranks(ev0.elapsed_time(ev1))
+    stats_mixed = {k: ctx.kernel_stats(k) for k in ctx.KERNELS}
+    ctx.profile(False)
     Pm = ctx.params
     mixed = {"value": job_rate(nc, args.steps, ms_mixed, world), "unit": UNIT,
              "ms_per_step": ms_mixed / args.steps,
@@ -548,17 +732,24 @@ def main():
              "what": "3-level V-cycle, FP64 fine CGKS, coarse levels smoothing the correction with the "
                      "FP32 linearised KFVS operator (precision 1)"}
     peak = cg.cgks_fp64_peak()
+    hbm = measured_hbm_peak()
     k_avg = k_ms / max(k_n, 1)
     roofline = {"bound": "alu", "kernel": "k_gks_points (FP64 gas-kinetic flux per Gauss point)",
                 "achieved": None, "peak": peak, "unit": "TFLOP/s", "frac": None,
                 "peak_source": "measured FP64 FMA-chain rate of this GPU (cgks_fp64_peak)",
-                "traffic": None, "kernel_ms": k_avg, "launches": k_n,
-                "other_kernels_ms": {"k_reconstruct": r_ms / max(r_n, 1), "k_gather": g_ms / max(g_n, 1)}}
+                "traffic": None, "kernel_ms": k_avg, "launches": k_n}
     if FLOP_PER_GP:
         ach = FLOP_PER_GP * ngp / (k_avg * 1e-3) / 1e12
         roofline.update(achieved=ach, frac=ach / peak, flop_per_gauss_point=FLOP_PER_GP)
     if DRAM_BYTES_PER_GP:
         roofline["traffic"] = DRAM_BYTES_PER_GP * ngp
+    kernels = kernel_rooflines(stats, args.steps, peak, hbm)
+    jvp = kernel_rooflines({"k_kfvs_jvp_faces": stats_mixed["k_kfvs_jvp_faces"],
+                            "k_kfvs_gather": stats_mixed["k_kfvs_gather"]}, args.steps, peak, hbm)
+    kernels["k_kfvs_jvp_faces"] = dict(jvp.get("k_kfvs_jvp_faces", {}), cycle="mixed")
+    kernels["k_kfvs_gather (mixed: FP64 and FP32 face fluxes)"] = dict(jvp.get("k_kfvs_gather", {}), cycle="mixed")
+    roofline["kernels"] = kernels
+    roofline["hbm_peak_source"] = "MEASURED_PEAKS.json hbm_gbs (copy bandwidth of this GPU pool)"
     launches = launches_per_vcycle({f: getattr(P, f) for f in ("dt_mode", "pre", "post", "n_levels", "coarse_steps",
                                                                "precision")})
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -571,11 +762,13 @@ def main():
                       "setup_s": setup_s, "params": {k: v for k, v in PARAMS.items()}},
            "e2e": e2e, "gpu_launches": launches * args.steps, "roofline": roofline, "clocks": clk.summary(),
            "mixed": mixed}
+    ctx.close()
+    if rank == 0 and world == 1 and not args.no_ramp:
+        out["ramp"] = run_ramp_throughput(cg, torch, args.steps, args.warmup)
     if rank == 0 and world == 1 and not args.no_converge:
-        out["converge"] = run_converge(cg, torch, args.converge_slab)
+        out["converge"] = run_converge(cg, torch, not args.no_converge_slab)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
-    ctx.close()
     if rank == 0:
         print(json.dumps(out))
     if world > 1:

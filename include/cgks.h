@@ -75,6 +75,11 @@ typedef struct {
   int32_t prolongation;    /* 0 injection (Sec. 4.2); 1 injection smoothed once over face neighbours: a
                               cell receives the volume-weighted mean of its own and its neighbours'
                               injected corrections (not in the paper) */
+  int32_t adjoint_recompute; /* transposed products of the adjoint (not in the paper): 0 (default) read
+                                the reconstruction's linearisation that cgks_linearize stores (2,220
+                                doubles per cell); 1 store nothing for the reconstruction and recompute
+                                its transposed product in every product (reverse mode through the WENO
+                                reconstruction of each cell, from the state at cgks_linearize) */
   uint64_t agglo_seed; /* 0: the paper's hash on cell ids; s > 0 relabels cell N as splitmix64(N ^ s) >> 33 */
 } cgks_params;
 
@@ -245,12 +250,22 @@ cgks_status cgks_adjoint(cgks_ctx* ctx, int component, const double* node_modes,
 cgks_status cgks_fp64_peak(double* tflops);
 
 /* Kernel timing for roofline measurement.  cgks_profile(ctx, 1) records CUDA events on the
- * context stream around every launch of the three fine-level kernels (0: Gauss-point gas-kinetic
- * flux, 1: reconstruction, 2: gather/update) until cgks_profile(ctx, 0).  cgks_kernel_stats
- * synchronises the stream and returns (host outputs) the summed device time in milliseconds and
- * the number of launches of kernel `which` recorded since profiling was enabled. */
+ * context stream around every launch of the kernels of the cycle until cgks_profile(ctx, 0), with
+ * the units each launch processes and its algorithmic DRAM bytes (every input read once, every
+ * output written once; the per-unit formulas are those of the kernels' documentation).  Kernel ids
+ * (`which`):
+ *   0 Gauss-point gas-kinetic flux (units: Gauss points)   1 reconstruction (cells)
+ *   2 fine gather / update (cells)                         3 coarse KFVS face fluxes (faces)
+ *   4 coarse KFVS gather (cells)                           5 coarse local time step (cells)
+ *   6 FAS forcing (cells)                                  7 coarse forward-Euler update (cells)
+ *   8 restriction (cells of the finer level)               9 prolongation (cells of the finer level)
+ *  10 FP32 KFVS directional derivative (faces)            11 residual norm (cells)
+ * cgks_kernel_stats synchronises the stream and returns (host outputs, each nullable) the summed
+ * device time in milliseconds, the number of launches, the summed units and the summed algorithmic
+ * bytes of kernel `which` recorded since profiling was enabled; an id outside 0..11 is CGKS_EINVAL. */
 cgks_status cgks_profile(cgks_ctx* ctx, int enable);
-cgks_status cgks_kernel_stats(cgks_ctx* ctx, int which, double* ms, int64_t* launches);
+cgks_status cgks_kernel_stats(cgks_ctx* ctx, int which, double* ms, int64_t* launches, double* units,
+                              double* bytes);
 
 /* Density-residual norm sqrt(mean_i (res_rho[i] / vol[i])^2) (the quantity cgks_residual reports)
  * for callers that cannot let the library allocate device memory: applications that hand each
@@ -263,7 +278,11 @@ cgks_status cgks_kernel_stats(cgks_ctx* ctx, int which, double* ms, int64_t* lau
  * first call on each device looks up that array's device address (cudaGetSymbolAddress); make
  * that first call before any stream capture.  All calls share the array: calls whose GPU work
  * overlaps (other streams, other host threads) race and may return wrong norms; serialise them.
- * Each call overwrites the partial sums it uses, so no clearing is needed between calls.  No
+ * Each call overwrites the partial sums it uses, so no clearing is needed between calls.  The
+ * looked-up address is kept per device index for the life of the process: after cudaDeviceReset,
+ * or when the device is used through a context other than its primary one, it no longer names the
+ * array, so do not call this entry point after either.  The result equals cgks_residual's norm to
+ * round-off (about 1e-15 relative), not bit for bit: the partial sums are grouped differently.  No
  * context is involved: on failure cgks_last_error(NULL) gives the message. */
 cgks_status cgks_density_norm_noalloc(const double* res_rho, const double* vol, int64_t n, void* cuda_stream,
                                       double* norm);

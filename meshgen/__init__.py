@@ -303,10 +303,11 @@ def wall_layout(nx=96, nz=64, first=1e-4, ratio=1.1, tet_min=0.5, tet_max=2.0):
     return z, n_prism
 
 
-def wall_box(nx=96, ny=64, nz=64, n_prism=None, first=1e-4, ratio=1.1, jitter=0.0, seed=2402):
+def wall_box(nx=96, ny=64, nz=64, n_prism=None, first=1e-4, ratio=1.1, jitter=0.0, seed=2402, outflow=BC_FARFIELD):
     """Laminar boundary-layer box: x in [0,1], y periodic with dy = dx, z from a no-slip wall
     (first spacing `first`, growth `ratio`, capped at twice dx), prism_z layers at the wall and
-    Kuhn tets above (wall_layout; n_prism overrides the count), farfield on x-in, x-out and top.
+    Kuhn tets above (wall_layout; n_prism overrides the count), farfield on x-in and top, and on x-out
+    the kind `outflow` (farfield, or BC_SUPER_OUT: the extrapolation outflow).
     96x64x64 -> 42 prism layers, height 0.374, 1,327,104 cells."""
     xs = np.linspace(0.0, 1.0, nx + 1)
     ys = np.arange(ny + 1) * (1.0 / nx)
@@ -314,7 +315,7 @@ def wall_box(nx=96, ny=64, nz=64, n_prism=None, first=1e-4, ratio=1.1, jitter=0.
     n_prism = npz if n_prism is None else n_prism
     return box_mesh(nx, ny, nz, layered_split(n_prism), xs=xs, ys=ys, zs=zs,
                     periodic=(False, True, False),
-                    bc=dict(xmin=BC_FARFIELD, xmax=BC_FARFIELD, zmin=BC_NOSLIP, zmax=BC_FARFIELD),
+                    bc=dict(xmin=BC_FARFIELD, xmax=outflow, zmin=BC_NOSLIP, zmax=BC_FARFIELD),
                     jitter=jitter, seed=seed,
                     jitter_mask=(lambda i, j, k: k > n_prism) if jitter > 0 else None)
 

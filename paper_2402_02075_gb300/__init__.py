@@ -42,7 +42,7 @@ class Params(C.Structure):
                 ("skew_min", C.c_double), ("sutherland", C.c_double), ("correction_relax", C.c_double), ("n_levels", C.c_int32), ("pre", C.c_int32), ("post", C.c_int32),
                 ("coarse_steps", C.c_int32), ("passes_per_level", C.c_int32), ("viscous", C.c_int32),
                 ("dt_mode", C.c_int32), ("precision", C.c_int32), ("coarse_smoother", C.c_int32), ("compression_factor", C.c_int32), ("prolongation", C.c_int32),
-                ("agglo_seed", C.c_uint64)]
+                ("adjoint_recompute", C.c_int32), ("agglo_seed", C.c_uint64)]
 
 
 def load(path: str = LIB_PATH):
@@ -83,7 +83,8 @@ def load(path: str = LIB_PATH):
                              C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double)],
             "cgks_fp64_peak": [C.POINTER(C.c_double)],
             "cgks_profile": [P, C.c_int],
-            "cgks_kernel_stats": [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)],
+            "cgks_kernel_stats": [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double),
+                                  C.POINTER(C.c_double)],
             "cgks_density_norm_noalloc": [d, d, C.c_int64, P, d],
             "cgks_last_error": [P],
         }
@@ -256,12 +257,17 @@ class Context:
     def profile(self, enable=True):
         _check(load().cgks_profile(self.h, int(bool(enable))), self.h)
 
+    KERNELS = ("k_gks_points", "k_reconstruct", "k_gather", "k_kfvs_faces", "k_kfvs_gather", "k_coarse_dt",
+               "k_forcing", "k_fe_update", "k_restrict", "k_prolong", "k_kfvs_jvp_faces", "k_norm")
+
     def kernel_stats(self, which):
-        """(total device ms, launches) of fine kernel `which` (0 Gauss-point flux, 1 reconstruction,
-        2 gather) since profiling was enabled."""
-        ms, n = C.c_double(), C.c_int64()
-        _check(load().cgks_kernel_stats(self.h, which, C.byref(ms), C.byref(n)), self.h)
-        return ms.value, n.value
+        """(total device ms, launches, units, algorithmic bytes) of kernel `which` (an index or a name
+        of KERNELS) since profiling was enabled."""
+        if isinstance(which, str):
+            which = self.KERNELS.index(which)
+        ms, n, u, b = C.c_double(), C.c_int64(), C.c_double(), C.c_double()
+        _check(load().cgks_kernel_stats(self.h, which, C.byref(ms), C.byref(n), C.byref(u), C.byref(b)), self.h)
+        return ms.value, n.value, u.value, b.value
 
     # ---- adjoint of the steady problem (compression_factor 0) ----
     def linearize(self):
@@ -316,23 +322,58 @@ def upload_mesh(mesh, params=None):
     return ctx
 
 
-def wall_force_function(ctx: Context, modes=None, component=1, **adjoint_kw):
-    """The wall force of the steady state that `ctx` holds as a torch function f(mach, amps) ->
-    J whose backward is the discrete adjoint (cgks_adjoint).  The state is the steady solution at the
-    context's Mach number with the mode amplitudes at zero, so f is evaluated and differentiated
-    there only: mach must equal that Mach number and amps be zero."""
+def _settle(ctx, tol=1e-10, chunk=200, max_steps=200000):
+    """Single-grid steps (cgks_step) until the density-residual norm is below `tol` and has stopped
+    falling (its chunk minimum no more than 10 % under the previous chunk's); returns the steps."""
+    steps, last = 0, float("inf")
+    while steps < max_steps:
+        h = ctx.step(chunk)
+        steps += chunk
+        if h[-1] < tol and h.min() > 0.9 * last:
+            return steps
+        last = min(last, float(h.min()))
+    raise CgksError(6, f"no steady state within {max_steps} steps (residual {h[-1]:.3e})")
+
+
+def wall_force_function(ctx: Context, mesh, modes=None, component=1, steady_tol=1e-10, max_steps=200000,
+                        **adjoint_kw):
+    """The wall force J(mach, amps) of the steady state as a torch function: forward sets the free-stream
+    Mach number, moves the nodes of `mesh` (a meshgen-style dict) by sum_k amps_k modes_k (re-uploading
+    it when the amplitudes change), runs single-grid steps from the context's current state to a steady
+    state (density-residual norm below steady_tol and no longer falling) and returns cgks_wall_force;
+    backward runs the discrete adjoint at that state (cgks_adjoint: dJ/dMach and dJ/d(mode amplitude)).
+    `ctx` holds `mesh` (or a displaced copy) and a state; compression_factor 0, local time steps."""
     import torch
+    modes_np = None if modes is None else np.ascontiguousarray(modes, dtype=np.float64)
+    n_modes = 0 if modes_np is None else len(modes_np)
+    current = {"amps": np.zeros(n_modes)}
+
+    def place(amps):
+        if np.array_equal(amps, current["amps"]):
+            return
+        W, G, a = ctx.state_get()
+        moved = dict(mesh)
+        moved["xyz"] = np.ascontiguousarray(mesh["xyz"] + np.tensordot(amps, modes_np, axes=1))
+        ctx.mesh_upload(moved)
+        ctx.state_init(W, G, a)
+        current["amps"] = amps.copy()
 
     class _WallForce(torch.autograd.Function):
         @staticmethod
         def forward(fctx, mach, amps):
-            assert abs(float(mach) - ctx.params.mach) <= 1e-15 * max(1.0, ctx.params.mach)
-            assert amps.numel() == (0 if modes is None else len(modes)) and not bool(torch.any(amps != 0))
+            a = amps.detach().cpu().numpy().astype(np.float64).reshape(-1)
+            if a.size != n_modes:
+                raise ValueError(f"expected {n_modes} mode amplitudes, got {a.size}")
+            prm = ctx.params
+            prm.mach = float(mach)
+            ctx.set_params(prm)
+            place(a)
+            _settle(ctx, steady_tol, max_steps=max_steps)
             return torch.tensor(ctx.wall_force(component), dtype=torch.float64)
 
         @staticmethod
         def backward(fctx, gout):
-            g = ctx.adjoint(component, modes, **adjoint_kw)
+            g = ctx.adjoint(component, modes_np, **adjoint_kw)
             s = float(gout)
             return (torch.tensor(s * g["dJ_dmach"], dtype=torch.float64),
                     torch.as_tensor(s * g["dJ_dmodes"], dtype=torch.float64))

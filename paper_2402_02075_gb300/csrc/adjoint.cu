@@ -65,6 +65,13 @@ __global__ void __launch_bounds__(512) k_vjp_slots(VjpArgs a) {
   for (int g = ty; g < 20 + 6 * 5; g += 16) vjp_slot_body(i, g, a, &cbs[0][tx], 32);
 }
 
+// the reconstruction's transposed product recomputed per cell (adjoint_recompute 1), in place of
+// k_vjp_slots
+__global__ void __launch_bounds__(128) k_vjp_recon(ReconArgs ra, VjpArgs a) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < a.nc) vjp_recon_body(i, ra, a, a.cbuf + i, a.nc);
+}
+
 __global__ void __launch_bounds__(128) k_vjp_cells(VjpArgs a) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < a.nc) vjp_cell_body(i, a);
@@ -221,7 +228,6 @@ static cgks_status adjoint_buffers(cgks_ctx* ctx) {
   const Fine& F = ctx->F;
   auto& M = ctx->mesh_allocs;
   CKS(dalloc(ctx, M, &ctx->Jp, (size_t)CGKS_PJ_IN * CGKS_PJ_OUT * F.ngp));
-  CKS(dalloc(ctx, M, &ctx->Jr, (size_t)CGKS_RJ_ROWS * F.nc));
   CKS(dalloc(ctx, M, &ctx->adt, F.nc));
   CKS(dalloc(ctx, M, &ctx->pbar, (size_t)CGKS_PB * F.ngp));
   CKS(dalloc(ctx, M, &ctx->aself, (size_t)20 * F.nc));
@@ -232,13 +238,25 @@ static cgks_status adjoint_buffers(cgks_ctx* ctx) {
   return CGKS_OK;
 }
 
+// the reconstruction's inputs at the linearisation point (adjoint_recompute 1): the copy of (W, grad W,
+// alpha) that cgks_linearize keeps
+static ReconArgs lin_recon_args(cgks_ctx* ctx) {
+  const Fine& F = ctx->F;
+  const int64_t nc = F.nc;
+  return ReconArgs{F.nc, F.nf, F.ctype, F.cf, F.fL, F.fR, F.ftag, F.cside, F.fnrm, F.Kop, F.ggw, F.lsw, F.aux, F.dtw,
+                   F.vol, ctx->aWG, ctx->aWG + 5 * nc, ctx->aWG + 20 * nc, nullptr, nullptr, make_phys(ctx->P), ctx->derr};
+}
+
 static cgks_status run_vjp(cgks_ctx* ctx, const double* rbar, const double* gbar, double* out) {
   const Fine& F = ctx->F;
   VjpArgs va{F.nc, F.nf, F.ngp, F.ctype, F.cside, F.cf, F.fL, F.fR, F.gp_face, F.gp_ptr, F.gp_x, F.gp_A, F.fshift,
              F.ctr, F.vol, ctx->adt, ctx->Jp, ctx->Jr, rbar, gbar, ctx->pbar, ctx->aself, ctx->arec, ctx->acb, out};
   k_vjp_points<<<grid_for(F.ngp, 128), 128, 0, ctx->stream>>>(va);
   k_vjp_coef<<<grid_for(F.nc, 128), 128, 0, ctx->stream>>>(va);
-  k_vjp_slots<<<grid_for(F.nc, 32), dim3(32, 16), 0, ctx->stream>>>(va);
+  if (ctx->lin_recompute)
+    k_vjp_recon<<<grid_for(F.nc, 128), 128, 0, ctx->stream>>>(lin_recon_args(ctx), va);
+  else
+    k_vjp_slots<<<grid_for(F.nc, 32), dim3(32, 16), 0, ctx->stream>>>(va);
   k_vjp_cells<<<grid_for(F.nc, 128), 128, 0, ctx->stream>>>(va);
   CK(cudaGetLastError());
   return CGKS_OK;
@@ -264,9 +282,19 @@ cgks_status cgks_linearize(cgks_ctx* ctx) {
   CKS(fine_fluxes(ctx, ctx->W, ctx->G, ctx->alpha));  // coefficients and time steps at the state
   ReconArgs ra{F.nc, F.nf, F.ctype, F.cf, F.fL, F.fR, F.ftag, F.cside, F.fnrm, F.Kop, F.ggw, F.lsw, F.aux, F.dtw,
                F.vol, ctx->W, ctx->G, ctx->alpha, ctx->rc, ctx->dt, ph, ctx->derr};
-  k_recon_jac<<<grid_for(F.nc, 128), 128, 0, ctx->stream>>>(ra, ctx->Jr);
+  ctx->lin_recompute = ctx->P.adjoint_recompute != 0;
+  if (ctx->lin_recompute) {
+    // keep the state; the reconstruction's transposed product is recomputed from it in every product
+    if (!ctx->aWG) CKS(dalloc(ctx, ctx->mesh_allocs, &ctx->aWG, (size_t)21 * F.nc));
+    CK(cudaMemcpyAsync(ctx->aWG, ctx->W, sizeof(double) * 5 * F.nc, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->aWG + 5 * F.nc, ctx->G, sizeof(double) * 15 * F.nc, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->aWG + 20 * F.nc, ctx->alpha, sizeof(double) * F.nc, cudaMemcpyDeviceToDevice, ctx->stream));
+  } else {
+    if (!ctx->Jr) CKS(dalloc(ctx, ctx->mesh_allocs, &ctx->Jr, (size_t)CGKS_RJ_ROWS * F.nc));
+    k_recon_jac<<<grid_for(F.nc, 128), 128, 0, ctx->stream>>>(ra, ctx->Jr);
+  }
   PointArgs pa{F.ngp, F.nf, F.nc, F.gp_face, F.fL, F.fR, F.ftag, F.gp_x, F.gp_A, F.fshift, F.ctr, ctx->rc,
-               ctx->dt, ctx->gpF, ctx->gpW, ctx->gpa, ph, ctx->derr};
+               ctx->dt, ctx->gpr, ph, ctx->derr};
   k_point_jac<<<grid_for(F.ngp, 128), 128, 0, ctx->stream>>>(pa, ctx->Jp);
   CK(cudaMemcpyAsync(ctx->adt, ctx->dt, sizeof(double) * F.nc, cudaMemcpyDeviceToDevice, ctx->stream));
   CK(cudaGetLastError());

@@ -131,6 +131,196 @@ HD void vjp_slot_body(int64_t i, int g, const VjpArgs& a, const double* cb, int 
 }
 
 
+// per cell, the reconstruction's part of the transposed product recomputed from the state instead of
+// read from the stored linearisation (adjoint_recompute 1).  cb (stride cs) holds the cotangents of
+// the cell's 50 coefficients and of its time step; out: the cotangents of its own (W, grad W) ->
+// self, and those of each interior neighbour's (W_q, grad W_q) -> the record of that face side.  The
+// reverse mode of reconstruct_cell written out step by step: per variable the WENO combination of
+// Sec. 3.4 (weights, smoothness indicators, the minimum in beta_1 taking the smaller branch and half
+// of each at a tie, as the forward-mode linearisation does), then the linear maps of p^2 (Sec. 3.1),
+// Green-Gauss and least squares; then the ghost states of boundary faces (a function of the cell's own
+// W and grad W: their transposed Jacobian from forward-mode duals) and the local time step.
+HD void vjp_recon_body(int64_t i, const ReconArgs& a, const VjpArgs& v, const double* cb, int64_t cs) {
+  const int64_t nc = a.nc, nf = a.nf;
+  const int nt = a.ctype[i] == 7 ? 5 : a.ctype[i];
+  const Phys& ph = a.ph;
+  double Q0[5], G0[15], self[20];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) Q0[q] = a.W[q * nc + i];
+#pragma unroll
+  for (int j = 0; j < 15; ++j) G0[j] = a.G[j * nc + i];
+#pragma unroll
+  for (int c = 0; c < 20; ++c) self[c] = 0.0;
+  // ghost states of boundary slots (primal) and their cotangents
+  double gval[6][20], gcot[6][20];
+  for (int m = 0; m < nt; ++m) {
+    const int64_t f = a.cf[(int64_t)m * nc + i];
+    for (int c = 0; c < 20; ++c) gcot[m][c] = 0.0;
+    if (a.fR[f] < 0) {
+      const double n[3] = {a.fnrm[f], a.fnrm[nf + f], a.fnrm[2 * nf + f]};
+      bc_ghost<double>(a.ftag[f], n, Q0, G0, gval[m], gval[m] + 5, ph.gamma, ph.Winf);
+    }
+  }
+  const double V23 = a.aux[i], V43 = a.aux[nc + i], al = a.alpha[i];
+  double M2[6];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) M2[j] = a.aux[(2 + j) * nc + i];
+  const double g1 = 0.5, g2 = 0.5;
+  for (int q = 0; q < 5; ++q) {
+    // stencil of variable q and the forward quantities
+    double Qn[6], Gn[6][3], b[9], gg[3] = {0, 0, 0}, gl[3] = {0, 0, 0};
+    for (int j = 0; j < 9; ++j) b[j] = 0.0;
+    for (int m = 0; m < nt; ++m) {
+      const int64_t f = a.cf[(int64_t)m * nc + i];
+      if (a.fR[f] >= 0) {
+        const int64_t nb = a.cside[(int64_t)m * nc + i] ? a.fL[f] : a.fR[f];
+        Qn[m] = a.W[q * nc + nb];
+        for (int e = 0; e < 3; ++e) Gn[m][e] = a.G[(3 * q + e) * nc + nb];
+      } else {
+        Qn[m] = gval[m][q];
+        for (int e = 0; e < 3; ++e) Gn[m][e] = gval[m][5 + 3 * q + e];
+      }
+      const double dQ = Qn[m] - Q0[q];
+      for (int j = 0; j < 9; ++j)
+        b[j] += a.Kop[(j * 24 + m) * nc + i] * dQ + a.Kop[(j * 24 + 6 + 3 * m) * nc + i] * Gn[m][0] +
+                a.Kop[(j * 24 + 7 + 3 * m) * nc + i] * Gn[m][1] + a.Kop[(j * 24 + 8 + 3 * m) * nc + i] * Gn[m][2];
+      for (int d = 0; d < 3; ++d) {
+        gg[d] += a.ggw[(3 * m + d) * nc + i] * (Qn[m] + Q0[q]);
+        gl[d] += a.lsw[(3 * m + d) * nc + i] * dQ;
+      }
+    }
+    const double a0 = Q0[q] - (b[3] * M2[0] + b[4] * M2[1] + b[5] * M2[2] + b[6] * M2[3] + b[7] * M2[4] + b[8] * M2[5]);
+    const double p1[3] = {al * gg[0], al * gg[1], al * gg[2]};
+    const double bGG = V23 * (p1[0] * p1[0] + p1[1] * p1[1] + p1[2] * p1[2]);
+    const double bLS = V23 * (gl[0] * gl[0] + gl[1] * gl[1] + gl[2] * gl[2]);
+    const double beta1 = fmin(bGG, bLS);
+    const double vv[3][3] = {{2.0 * b[3], b[6], b[8]}, {b[6], 2.0 * b[4], b[7]}, {b[8], b[7], 2.0 * b[5]}};
+    double first = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      const double* x = vv[d];
+      first += b[d] * b[d] + M2[0] * x[0] * x[0] + M2[1] * x[1] * x[1] + M2[2] * x[2] * x[2] +
+               2.0 * (M2[3] * x[0] * x[1] + M2[4] * x[1] * x[2] + M2[5] * x[0] * x[2]);
+    }
+    const double second = 4.0 * (b[3] * b[3] + b[4] * b[4] + b[5] * b[5]) + b[6] * b[6] + b[7] * b[7] + b[8] * b[8];
+    const double beta2 = V23 * first + V43 * second;
+    const double rden = 1.0 / (Q0[q] * Q0[q] + beta1 + 1e-40);
+    const double bt1 = beta1 * rden, bt2 = beta2 * rden, dif = bt2 - bt1;
+    const double d1 = ph.weno_eps + bt1, d2 = ph.weno_eps + bt2;
+    const double s2 = dif * dif, d11 = d1 * d1, d22 = d2 * d2;
+    const double A1 = g1 * (d11 + s2) * d22, A2 = g2 * (d22 + s2) * d11;
+    const double inv = 1.0 / (A1 + A2);
+    const double w1 = A1 * inv, w2 = A2 * inv;
+    const double c2 = w2 * (1.0 / g2), c1 = w1 - w2 * (g1 / g2);
+    // reverse: out[0] = c2 a0 + c1 Q0, out[1+d] = c2 b[d] + c1 p1[d] (d < 3), out[1+j] = c2 b[j] (j >= 3)
+    double ob[10];
+    for (int k = 0; k < 10; ++k) ob[k] = cb[(10 * q + k) * cs];
+    double c2b = ob[0] * a0, c1b = ob[0] * Q0[q];
+    for (int d = 0; d < 3; ++d) {
+      c2b += ob[1 + d] * b[d];
+      c1b += ob[1 + d] * p1[d];
+    }
+    for (int j = 3; j < 9; ++j) c2b += ob[1 + j] * b[j];
+    const double a0b = c2 * ob[0];
+    double q0b = c1 * ob[0];
+    double bb[9], p1b[3];
+    for (int d = 0; d < 3; ++d) {
+      bb[d] = c2 * ob[1 + d];
+      p1b[d] = c1 * ob[1 + d];
+    }
+    for (int j = 3; j < 9; ++j) bb[j] = c2 * ob[1 + j];
+    // weights
+    const double w1b = c1b, w2b = c2b * (1.0 / g2) - c1b * (g1 / g2);
+    const double t = w1b * w1 + w2b * w2;
+    const double A1b = inv * (w1b - t), A2b = inv * (w2b - t);
+    const double d11b = A1b * g1 * d22 + A2b * g2 * (d22 + s2);
+    const double d22b = A1b * g1 * (d11 + s2) + A2b * g2 * d11;
+    const double s2b = A1b * g1 * d22 + A2b * g2 * d11;
+    const double bt1b = 2.0 * d1 * d11b - 2.0 * dif * s2b, bt2b = 2.0 * d2 * d22b + 2.0 * dif * s2b;
+    double beta1b = bt1b * rden;
+    const double beta2b = bt2b * rden;
+    const double rdenb = bt1b * beta1 + bt2b * beta2;
+    q0b += -rden * rden * 2.0 * Q0[q] * rdenb;
+    beta1b += -rden * rden * rdenb;
+    // smoothness indicator of p^2
+    const double firstb = V23 * beta2b, secondb = V43 * beta2b;
+    double vb[3][3];
+    for (int d = 0; d < 3; ++d) {
+      const double* x = vv[d];
+      bb[d] += 2.0 * b[d] * firstb;
+      vb[d][0] = firstb * (2.0 * M2[0] * x[0] + 2.0 * M2[3] * x[1] + 2.0 * M2[5] * x[2]);
+      vb[d][1] = firstb * (2.0 * M2[1] * x[1] + 2.0 * M2[3] * x[0] + 2.0 * M2[4] * x[2]);
+      vb[d][2] = firstb * (2.0 * M2[2] * x[2] + 2.0 * M2[4] * x[1] + 2.0 * M2[5] * x[0]);
+    }
+    bb[3] += 2.0 * vb[0][0] + 8.0 * b[3] * secondb;
+    bb[4] += 2.0 * vb[1][1] + 8.0 * b[4] * secondb;
+    bb[5] += 2.0 * vb[2][2] + 8.0 * b[5] * secondb;
+    bb[6] += vb[0][1] + vb[1][0] + 2.0 * b[6] * secondb;
+    bb[7] += vb[1][2] + vb[2][1] + 2.0 * b[7] * secondb;
+    bb[8] += vb[0][2] + vb[2][0] + 2.0 * b[8] * secondb;
+    // beta_1 = min(beta_GG, beta_LS)
+    const double bGGb = bGG < bLS ? beta1b : (bGG > bLS ? 0.0 : 0.5 * beta1b);
+    const double bLSb = bGG < bLS ? 0.0 : (bGG > bLS ? beta1b : 0.5 * beta1b);
+    double glb[3], ggb[3];
+    for (int d = 0; d < 3; ++d) {
+      p1b[d] += 2.0 * V23 * p1[d] * bGGb;
+      glb[d] = 2.0 * V23 * gl[d] * bLSb;
+      ggb[d] = al * p1b[d];
+    }
+    // a0 = Q0 - sum_j b_j M2_j
+    q0b += a0b;
+    for (int j = 3; j < 9; ++j) bb[j] -= a0b * M2[j - 3];
+    // the linear maps, slot by slot
+    for (int m = 0; m < nt; ++m) {
+      const int64_t f = a.cf[(int64_t)m * nc + i];
+      double dQb = 0.0, Gnb[3] = {0, 0, 0};
+      for (int j = 0; j < 9; ++j) {
+        dQb += a.Kop[(j * 24 + m) * nc + i] * bb[j];
+        for (int e = 0; e < 3; ++e) Gnb[e] += a.Kop[(j * 24 + 6 + 3 * m + e) * nc + i] * bb[j];
+      }
+      double ggsum = 0.0;
+      for (int d = 0; d < 3; ++d) {
+        dQb += a.lsw[(3 * m + d) * nc + i] * glb[d];
+        ggsum += a.ggw[(3 * m + d) * nc + i] * ggb[d];
+      }
+      const double Qnb = dQb + ggsum;
+      q0b += ggsum - dQb;
+      if (a.fR[f] >= 0) {
+        double* rec = v.rec + (2 * f + a.cside[(int64_t)m * nc + i]) * 20;
+        rec[q] = Qnb;
+        for (int e = 0; e < 3; ++e) rec[5 + 3 * q + e] = Gnb[e];
+      } else {
+        gcot[m][q] += Qnb;
+        for (int e = 0; e < 3; ++e) gcot[m][5 + 3 * q + e] += Gnb[e];
+      }
+    }
+    self[q] += q0b;
+  }
+  // ghost states: their transposed Jacobian in the cell's own (W, grad W), one dual seed per input
+  for (int m = 0; m < nt; ++m) {
+    const int64_t f = a.cf[(int64_t)m * nc + i];
+    if (a.fR[f] >= 0) continue;
+    const DualD n[3] = {DualD(a.fnrm[f]), DualD(a.fnrm[nf + f]), DualD(a.fnrm[2 * nf + f])};
+    for (int c = 0; c < 20; ++c) {
+      DualD Wd[5], Gd[15], Wg[5], Gg[15];
+      for (int q = 0; q < 5; ++q) Wd[q] = DualD(Q0[q], c == q ? 1.0 : 0.0);
+      for (int j = 0; j < 15; ++j) Gd[j] = DualD(G0[j], c == 5 + j ? 1.0 : 0.0);
+      bc_ghost<DualD>(a.ftag[f], n, Wd, Gd, Wg, Gg, DualD(ph.gamma), ph.Winf);
+      double sacc = 0.0;
+      for (int q = 0; q < 5; ++q) sacc += Wg[q].d * gcot[m][q];
+      for (int j = 0; j < 15; ++j) sacc += Gg[j].d * gcot[m][5 + j];
+      self[c] += sacc;
+    }
+  }
+  // local time step
+  const double dtb = cb[CGKS_RC * cs];
+  for (int c = 0; c < 5; ++c) {
+    DualD Qd[5];
+    for (int q = 0; q < 5; ++q) Qd[q] = DualD(Q0[q], q == c ? 1.0 : 0.0);
+    self[c] += time_step<DualD>(i, a, Qd).d * dtb;
+  }
+  for (int c = 0; c < 20; ++c) v.self[(int64_t)c * nc + i] = self[c];
+}
+
 // per cell: own part plus the records its neighbours wrote for it -> cotangents of its (W, G)
 HD void vjp_cell_body(int64_t i, const VjpArgs& a) {
   const int64_t nc = a.nc;

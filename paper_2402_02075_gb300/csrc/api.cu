@@ -174,12 +174,12 @@ static cudaEvent_t take_event(cgks_ctx* c) {
   return e;
 }
 
-ProfScope::ProfScope(cgks_ctx* ctx, int kind) : c(ctx), k(kind) {
+ProfScope::ProfScope(cgks_ctx* ctx, int kind, double units, double bytes) : c(ctx), k(kind) {
   if (!c->prof) return;
   cudaEvent_t e0 = take_event(c);
   e1 = take_event(c);
   cudaEventRecord(e0, c->stream);
-  c->prof_ev[k].push_back({e0, e1});
+  c->prof_ev[k].push_back({e0, e1, units, bytes});
 }
 
 ProfScope::~ProfScope() {
@@ -189,8 +189,8 @@ ProfScope::~ProfScope() {
 static void release_events(cgks_ctx* c) {
   for (auto& v : c->prof_ev) {
     for (auto& p : v) {
-      c->ev_pool.push_back(p.first);
-      c->ev_pool.push_back(p.second);
+      c->ev_pool.push_back(p.e0);
+      c->ev_pool.push_back(p.e1);
     }
     v.clear();
   }
@@ -208,18 +208,23 @@ cgks_status cgks_profile(cgks_ctx* ctx, int enable) {
   return CGKS_OK;
 }
 
-cgks_status cgks_kernel_stats(cgks_ctx* ctx, int which, double* ms, int64_t* launches) {
+cgks_status cgks_kernel_stats(cgks_ctx* ctx, int which, double* ms, int64_t* launches, double* units,
+                              double* bytes) {
   if (!ctx) return CGKS_EINVAL;
-  if (which < 0 || which > 2) return cgks_fail(ctx, CGKS_EINVAL, "kernel id must be 0, 1 or 2");
+  if (which < 0 || which >= PK_COUNT) return cgks_fail(ctx, CGKS_EINVAL, "kernel id out of range");
   CK(cudaStreamSynchronize(ctx->stream));
-  double total = 0.0;
+  double total = 0.0, u = 0.0, b = 0.0;
   for (auto& p : ctx->prof_ev[which]) {
     float t = 0.f;
-    CK(cudaEventElapsedTime(&t, p.first, p.second));
+    CK(cudaEventElapsedTime(&t, p.e0, p.e1));
     total += t;
+    u += p.units;
+    b += p.bytes;
   }
   if (ms) *ms = total;
   if (launches) *launches = (int64_t)ctx->prof_ev[which].size();
+  if (units) *units = u;
+  if (bytes) *bytes = b;
   return CGKS_OK;
 }
 
@@ -263,6 +268,8 @@ static cgks_status check_params(cgks_ctx* ctx, const cgks_params* p) {
   if (p->compression_factor != 0 && p->compression_factor != 1)
     return cgks_fail(ctx, CGKS_EINVAL, "compression_factor must be 0 or 1");
   if (p->prolongation != 0 && p->prolongation != 1) return cgks_fail(ctx, CGKS_EINVAL, "prolongation must be 0 or 1");
+  if (p->adjoint_recompute != 0 && p->adjoint_recompute != 1)
+    return cgks_fail(ctx, CGKS_EINVAL, "adjoint_recompute must be 0 or 1");
   return CGKS_OK;
 }
 
@@ -342,7 +349,8 @@ cgks_status cgks_mesh_upload(cgks_ctx* ctx, int64_t n_nodes, const double* xyz, 
   free_list(ctx->mesh_allocs);
   // the adjoint's arrays were in mesh_allocs
   ctx->Jp = ctx->Jr = ctx->adt = ctx->pbar = ctx->aself = ctx->arec = ctx->avec = ctx->apart = ctx->akry = nullptr;
-  ctx->ajc = ctx->acb = nullptr;
+  ctx->ajc = ctx->acb = ctx->aWG = nullptr;
+  ctx->lin_recompute = false;
   ctx->F = Fine();
   ctx->L.clear();
   ctx->C.clear();
@@ -368,9 +376,7 @@ cgks_status cgks_mesh_upload(cgks_ctx* ctx, int64_t n_nodes, const double* xyz, 
   CKS(dalloc(ctx, M, &ctx->rc, (size_t)CGKS_RC * F.nc));
   CKS(dalloc(ctx, M, &ctx->dt, F.nc));
   CKS(dalloc(ctx, M, &ctx->res, 5 * F.nc));
-  CKS(dalloc(ctx, M, &ctx->gpF, 5 * F.ngp));
-  CKS(dalloc(ctx, M, &ctx->gpW, 5 * F.ngp));
-  CKS(dalloc(ctx, M, &ctx->gpa, F.ngp));
+  CKS(dalloc(ctx, M, &ctx->gpr, (size_t)CGKS_GPR * F.ngp));
   CKS(dalloc(ctx, M, &ctx->ffl, 5 * F.nf));
   CKS(dalloc(ctx, M, &ctx->ffl32, 5 * F.nf));
   CK(cudaStreamSynchronize(ctx->stream));

@@ -234,6 +234,9 @@ static void prolong(cgks_ctx* ctx, int lev_fine, const int32_t* f2c, int64_t ncc
                     const double* Wc0, double* Wf) {
   const Level& L = ctx->L[lev_fine];
   cudaStream_t st = ctx->stream;
+  ProfScope ps(ctx, PK_PROLONG, (double)L.nc,
+               L.nc * 84.0 + ncc * 80.0 +
+                   (ctx->P.prolongation == 1 ? (L.nf + L.n_int + L.n_per) * 4.0 + L.nf * 8.0 + L.nc * 12.0 : 0.0));
   if (ctx->P.prolongation == 1)
     k_prolong_smooth<<<grid_for(L.nc, 256), 256, 0, st>>>(L.nc, ncc, L.c2f_ptr, L.c2f, L.fL, L.fR, L.vol, f2c, Wc, Wc0,
                                                            Wf, ctx->P.gamma, ctx->P.correction_relax,
@@ -270,6 +273,7 @@ __global__ void k_norm_final(int nparts, int64_t n, const double* __restrict__ p
 
 cgks_status density_norm(cgks_ctx* ctx, const double* res, const double* vol, int64_t n, double* out_dev) {
   const int parts = 304;
+  ProfScope ps(ctx, PK_NORM, (double)n, n * 16.0);
   k_norm_partial<<<parts, 256, 0, ctx->stream>>>(n, res, vol, ctx->nrm_part);
   k_norm_final<<<1, 32, 0, ctx->stream>>>(parts, n, ctx->nrm_part, out_dev);
   CK(cudaGetLastError());
@@ -283,8 +287,17 @@ cgks_status kfvs_residual(cgks_ctx* ctx, int lev, const double* W, double* res) 
   const Level& L = ctx->L[lev];
   const Phys ph = make_phys(ctx->P);
   double* ff = lev == 0 ? ctx->ffl : ctx->C[lev].ff;
-  k_kfvs_faces<<<grid_for(L.nf, 256), 256, 0, ctx->stream>>>(L.nf, L.fL, L.fR, L.ftag, L.Sn, L.nc, W, ff, ph, ctx->derr);
-  k_kfvs_gather<double><<<grid_for(L.nc, 256), 256, 0, ctx->stream>>>(L.nc, L.nf, L.c2f_ptr, L.c2f, L.fL, L.fR, ff, res);
+  const double entries = (double)(L.nf + L.n_int + L.n_per);
+  {
+    ProfScope ps(ctx, PK_KFVS_FACES, (double)L.nf, L.nf * 76.0 + L.nc * 40.0);
+    k_kfvs_faces<<<grid_for(L.nf, 256), 256, 0, ctx->stream>>>(L.nf, L.fL, L.fR, L.ftag, L.Sn, L.nc, W, ff, ph,
+                                                                ctx->derr);
+  }
+  {
+    ProfScope ps(ctx, PK_KFVS_GATHER, (double)L.nc, L.nc * 44.0 + entries * 4.0 + L.nf * 48.0);
+    k_kfvs_gather<double><<<grid_for(L.nc, 256), 256, 0, ctx->stream>>>(L.nc, L.nf, L.c2f_ptr, L.c2f, L.fL, L.fR, ff,
+                                                                         res);
+  }
   CK(cudaGetLastError());
   return CGKS_OK;
 }
@@ -293,17 +306,28 @@ cgks_status kfvs_jvp(cgks_ctx* ctx, int lev, const double* W0, const double* X, 
   const Level& L = ctx->L[lev];
   const Phys ph = make_phys(ctx->P);
   float* ff = lev == 0 ? ctx->ffl32 : ctx->C[lev].ff32;
-  k_kfvs_jvp_faces<<<grid_for(L.nf, 256), 256, 0, ctx->stream>>>(L.nf, L.fL, L.fR, L.ftag, L.Sn, L.nc, W0, X,
-                                                                  x_is_state, ff, ph, ctx->derr);
-  k_kfvs_gather<float><<<grid_for(L.nc, 256), 256, 0, ctx->stream>>>(L.nc, L.nf, L.c2f_ptr, L.c2f, L.fL, L.fR, ff, res);
+  const double entries = (double)(L.nf + L.n_int + L.n_per);
+  {
+    ProfScope ps(ctx, PK_KFVS_JVP, (double)L.nf, L.nf * 56.0 + L.nc * 80.0);
+    k_kfvs_jvp_faces<<<grid_for(L.nf, 256), 256, 0, ctx->stream>>>(L.nf, L.fL, L.fR, L.ftag, L.Sn, L.nc, W0, X,
+                                                                    x_is_state, ff, ph, ctx->derr);
+  }
+  {
+    ProfScope ps(ctx, PK_KFVS_GATHER, (double)L.nc, L.nc * 44.0 + entries * 4.0 + L.nf * 28.0);
+    k_kfvs_gather<float><<<grid_for(L.nc, 256), 256, 0, ctx->stream>>>(L.nc, L.nf, L.c2f_ptr, L.c2f, L.fL, L.fR, ff,
+                                                                        res);
+  }
   CK(cudaGetLastError());
   return CGKS_OK;
 }
 
 cgks_status coarse_dt(cgks_ctx* ctx, int lev, const double* W, double* dt) {
   const Level& L = ctx->L[lev];
-  k_coarse_dt<<<grid_for(L.nc, 256), 256, 0, ctx->stream>>>(L.nc, L.nf, L.c2f_ptr, L.c2f, L.Sn, L.area, L.vol, W, dt,
-                                                            ctx->P.gamma, ctx->P.cfl_coarse);
+  {
+    ProfScope ps(ctx, PK_COARSE_DT, (double)L.nc, L.nc * 60.0 + (L.nf + L.n_int + L.n_per) * 4.0 + L.nf * 32.0);
+    k_coarse_dt<<<grid_for(L.nc, 256), 256, 0, ctx->stream>>>(L.nc, L.nf, L.c2f_ptr, L.c2f, L.Sn, L.area, L.vol, W,
+                                                              dt, ctx->P.gamma, ctx->P.cfl_coarse);
+  }
   if (ctx->P.dt_mode == 1) CKS(global_min_dt(ctx, dt, L.nc));
   CK(cudaGetLastError());
   return CGKS_OK;
@@ -326,8 +350,11 @@ static cgks_status coarse_smooth(cgks_ctx* ctx, int l) {
   CoarseBuf& B = ctx->C[l];
   CKS(coarse_dt(ctx, l, B.W, B.dt));
   if (ctx->P.coarse_smoother == 1) return lusgs_step(ctx, l);
-  k_fe_update<<<grid_for(L.nc, 256), 256, 0, ctx->stream>>>(L.nc, B.dt, L.vol, B.R, B.F, B.W, ctx->P.gamma,
-                                                             (unsigned long long*)ctx->d_skipped, ctx->derr);
+  {
+    ProfScope ps(ctx, PK_FE_UPDATE, (double)L.nc, L.nc * 176.0);
+    k_fe_update<<<grid_for(L.nc, 256), 256, 0, ctx->stream>>>(L.nc, B.dt, L.vol, B.R, B.F, B.W, ctx->P.gamma,
+                                                               (unsigned long long*)ctx->d_skipped, ctx->derr);
+  }
   CK(cudaGetLastError());
   return CGKS_OK;
 }
@@ -345,6 +372,7 @@ static cgks_status coarse_cycle(cgks_ctx* ctx, int l) {
     CK(cudaMemsetAsync(B.R, 0, sizeof(double) * n5, st));
   } else {
     CKS(kfvs_residual(ctx, l, B.W, B.R));
+    ProfScope ps(ctx, PK_FORCING, (double)L.nc, n5 * 24.0);
     k_forcing<<<grid_for(n5, 256), 256, 0, st>>>(n5, B.Rs, B.R, B.F);
   }
   for (int s = 0; s < ctx->P.coarse_steps; ++s) {
@@ -355,8 +383,11 @@ static cgks_status coarse_cycle(cgks_ctx* ctx, int l) {
     const Level& Cn = ctx->L[l + 1];
     CoarseBuf& N = ctx->C[l + 1];
     CKS(coarse_residual(ctx, l));
-    k_restrict<<<grid_for(Cn.nc, 256), 256, 0, st>>>(Cn.nc, L.nc, Cn.agg_ptr, Cn.agg, L.vol, Cn.vol, B.W, B.R, B.F,
-                                                     N.W, N.Rs);
+    {
+      ProfScope ps(ctx, PK_RESTRICT, (double)L.nc, L.nc * 132.0 + Cn.nc * 92.0);
+      k_restrict<<<grid_for(Cn.nc, 256), 256, 0, st>>>(Cn.nc, L.nc, Cn.agg_ptr, Cn.agg, L.vol, Cn.vol, B.W, B.R, B.F,
+                                                       N.W, N.Rs);
+    }
     CK(cudaMemcpyAsync(N.W0, N.W, sizeof(double) * 5 * Cn.nc, cudaMemcpyDeviceToDevice, st));
     CKS(coarse_cycle(ctx, l + 1));
     prolong(ctx, l, Cn.f2c, Cn.nc, N.W, N.W0, B.W);
@@ -390,8 +421,11 @@ cgks_status vcycle_once(cgks_ctx* ctx, double* norm_dev) {
   // defect at the smoothed state (gradient and compression outputs discarded)
   CKS(fine_fluxes(ctx, ctx->W, ctx->G, ctx->alpha));
   CKS(fine_gather(ctx, ctx->W, nullptr, ctx->res, nullptr, nullptr, 0));
-  k_restrict<<<grid_for(C1.nc, 256), 256, 0, st>>>(C1.nc, F.nc, C1.agg_ptr, C1.agg, ctx->L0c.vol, C1.vol, ctx->W, ctx->res,
-                                                   nullptr, B1.W, B1.Rs);
+  {
+    ProfScope ps(ctx, PK_RESTRICT, (double)F.nc, F.nc * 92.0 + C1.nc * 92.0);
+    k_restrict<<<grid_for(C1.nc, 256), 256, 0, st>>>(C1.nc, F.nc, C1.agg_ptr, C1.agg, ctx->L0c.vol, C1.vol, ctx->W,
+                                                     ctx->res, nullptr, B1.W, B1.Rs);
+  }
   CK(cudaMemcpyAsync(B1.W0, B1.W, sizeof(double) * 5 * C1.nc, cudaMemcpyDeviceToDevice, st));
   CKS(coarse_cycle(ctx, 1));
   prolong(ctx, 0, C1.f2c, C1.nc, B1.W, B1.W0, ctx->W);

@@ -11,9 +11,83 @@ __global__ void __launch_bounds__(128) k_gks_points(PointArgs a) {
   if (g < a.ngp) gks_point_body(g, a);
 }
 
-__global__ void __launch_bounds__(128) k_gather(GatherArgs a) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < a.nc) gather_body(i, a);
+// ---- gather: per cell, fixed-order sums of its faces' Gauss-point records ----------------------
+//
+// One thread per cell, 32 cells per warp.  The records of a face are contiguous (3 or 4 records of
+// 112 bytes), so for each local-face slot the warp copies the 32 faces' records into shared memory
+// with 16-byte cp.async copies, lanes of one copy instruction covering one face's contiguous bytes
+// (coalesced), and each thread then sums its own face from shared memory in ascending point order
+// (gather_face, the same arithmetic and order as gather_body).  The copies of slot m + 1 are in
+// flight while slot m is summed (two buffers per warp).
+
+#define GATHER_WARPS 2                      // warps per block
+#define GATHER_FACE_DOUBLES (4 * CGKS_GPR)  // room for the records of one face: 448 bytes
+#define GATHER_SMEM (GATHER_WARPS * 2 * 32 * GATHER_FACE_DOUBLES * (int)sizeof(double))
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+__global__ void __launch_bounds__(32 * GATHER_WARPS) k_gather(GatherArgs a) {
+  extern __shared__ __align__(16) double gsm[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t nc = a.nc;
+  const int64_t i = ((int64_t)blockIdx.x * GATHER_WARPS + w) * 32 + lane;
+  const bool valid = i < nc;
+  const int nt = valid ? (a.ctype[i] == 7 ? 5 : a.ctype[i]) : 0;  // pyramids (type 7) have 5 faces
+  const int nmax = __reduce_max_sync(0xffffffffu, nt);
+  double* const buf0 = gsm + (size_t)(2 * w) * 32 * GATHER_FACE_DOUBLES;  // buffers of slots 0, 2, 4
+  double* const buf1 = buf0 + 32 * GATHER_FACE_DOUBLES;                    // and of slots 1, 3, 5
+  // face slot m of this lane's cell: first record, number of records, side sign
+  auto slot = [&](int m, int64_t& g0, int& ng, bool& sg) {
+    g0 = 0;
+    ng = 0;
+    sg = false;
+    if (m < nt) {
+      const int64_t f = a.cf[(int64_t)m * nc + i];
+      sg = a.cside[(int64_t)m * nc + i] != 0;
+      g0 = a.gp_ptr[f];
+      ng = (int)(a.gp_ptr[f + 1] - g0);
+    }
+  };
+  // the 32 faces of one slot into buffer b: face j's 7 x ng 16-byte chunks by lanes 0 .. 7 ng - 1
+  auto issue = [&](double* b, int64_t g0, int ng) {
+    for (int j = 0; j < 32; ++j) {
+      const int64_t gj = __shfl_sync(0xffffffffu, g0, j);
+      const int nj = __shfl_sync(0xffffffffu, ng, j);
+      if (lane < (CGKS_GPR / 2) * nj) cp_async16(b + j * GATHER_FACE_DOUBLES + 2 * lane, a.gpr + CGKS_GPR * gj + 2 * lane);
+    }
+    cp_async_commit();
+  };
+  GatherAcc c;
+  gather_init(c);
+  int64_t g0;
+  int ng;
+  bool sg;
+  slot(0, g0, ng, sg);
+  if (nmax > 0) issue(buf0, g0, ng);
+  for (int m = 0; m < nmax; ++m) {
+    int64_t g1 = 0;
+    int n1 = 0;
+    bool s1 = false;
+    if (m + 1 < nmax) {
+      slot(m + 1, g1, n1, s1);
+      issue((m & 1) ? buf0 : buf1, g1, n1);
+    } else {
+      cp_async_commit();  // an empty group keeps "all but the newest group" meaning slot m
+    }
+    cp_async_wait_one();
+    __syncwarp();
+    if (ng > 0) gather_face(((m & 1) ? buf1 : buf0) + lane * GATHER_FACE_DOUBLES, ng, sg, c);
+    __syncwarp();  // every lane is done with buffer m & 1 before slot m + 2 is copied into it
+    g0 = g1;
+    ng = n1;
+    sg = s1;
+  }
+  if (valid) gather_store(i, a, c);
 }
 
 // global minimum time step (dt_mode 1): fixed-order two-stage reduction, then broadcast
@@ -55,15 +129,16 @@ cgks_status fine_fluxes(cgks_ctx* ctx, const double* W, const double* G, const d
   const Phys ph = make_phys(ctx->P);
   ReconArgs ra{F.nc, F.nf, F.ctype, F.cf, F.fL, F.fR, F.ftag, F.cside, F.fnrm, F.Kop, F.ggw, F.lsw, F.aux, F.dtw,
                F.vol, W, G, alpha, ctx->rc, ctx->dt, ph, ctx->derr};
+  const double slots = (double)(F.nf + F.n_int + F.n_per);
   {
-    ProfScope ps(ctx, 1);
+    ProfScope ps(ctx, PK_RECON, (double)F.nc, F.nc * (306.0 * 8 + 1 + 51.0 * 8) + slots * 5 + F.nf * 36.0);
     k_reconstruct<<<grid_for(F.nc, 128), 128, 0, ctx->stream>>>(ra);
   }
   if (ctx->P.dt_mode == 1) CKS(global_min_dt(ctx, ctx->dt, F.nc));
   PointArgs pa{F.ngp, F.nf, F.nc, F.gp_face, F.fL, F.fR, F.ftag, F.gp_x, F.gp_A, F.fshift, F.ctr, ctx->rc,
-               ctx->dt, ctx->gpF, ctx->gpW, ctx->gpa, ph, ctx->derr};
+               ctx->dt, ctx->gpr, ph, ctx->derr};
   {
-    ProfScope ps(ctx, 0);
+    ProfScope ps(ctx, PK_POINTS, (double)F.ngp, F.ngp * (52.0 + 8.0 * CGKS_GPR) + F.nf * 36.0 + F.nc * 432.0);
     k_gks_points<<<grid_for(F.ngp, 128), 128, 0, ctx->stream>>>(pa);
   }
   CK(cudaGetLastError());
@@ -73,11 +148,19 @@ cgks_status fine_fluxes(cgks_ctx* ctx, const double* W, const double* G, const d
 cgks_status fine_gather(cgks_ctx* ctx, const double* W_in, double* W_out, double* res, double* G_out,
                         double* alpha_out, int update) {
   const Fine& F = ctx->F;
-  GatherArgs ga{F.nc, F.ngp, F.ctype, F.cside, F.cf, F.gp_ptr, F.gp_A, ctx->gpF, ctx->gpW, ctx->gpa, F.vol,
+  GatherArgs ga{F.nc, F.ngp, F.ctype, F.cside, F.cf, F.gp_ptr, ctx->gpr, F.vol,
                 ctx->dt, W_in, W_out, res, G_out, alpha_out, update, ctx->P.gamma, ctx->derr};
   {
-    ProfScope ps(ctx, 2);
-    k_gather<<<grid_for(F.nc, 128), 128, 0, ctx->stream>>>(ga);
+    const double per_cell = 1 + 8 + (update ? 88 : 0) + (res ? 40 : 0) + (G_out ? 120 : 0) + (alpha_out ? 8 : 0);
+    ProfScope ps(ctx, PK_GATHER, (double)F.nc,
+                 F.nc * per_cell + (F.nf + F.n_int + F.n_per) * 5.0 + F.nf * 4.0 + F.ngp * 8.0 * CGKS_GPR);
+    static bool smem_set = false;  // the kernel's dynamic shared memory exceeds the 48 KiB default
+    if (!smem_set) {
+      CK(cudaFuncSetAttribute(k_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, GATHER_SMEM));
+      smem_set = true;
+    }
+    const int64_t per_block = 32 * GATHER_WARPS;
+    k_gather<<<(unsigned)((F.nc + per_block - 1) / per_block), 32 * GATHER_WARPS, GATHER_SMEM, ctx->stream>>>(ga);
   }
   CK(cudaGetLastError());
   return CGKS_OK;

@@ -15,6 +15,8 @@
 // time derivatives from Euler-flux Jacobian products (the derivative of an equilibrium moment along
 // a slope direction).
 #pragma once
+#include <cstring>
+
 #include "internal.cuh"
 #include "kinetic.cuh"
 
@@ -505,7 +507,7 @@ struct PointArgs {
   int64_t ngp, nf, nc;
   const int32_t *gp_face, *fL, *fR, *ftag;
   const double *gp_x, *gp_A, *fshift, *ctr, *rc, *dt;
-  double *gpF, *gpW, *gpa;
+  double* gpr;  // [ngp][CGKS_GPR] records: flux x weight / dt (5), interface state (5), area vector (3), alpha
   Phys ph;
   DevErr* err;
 };
@@ -696,12 +698,15 @@ HD void gks_point_body(int64_t g, const PointArgs& a) {
   double Fg[5], Wg[5], alpha;
   point_flux<double>(p.n, p.iw, p.R < 0, a.ftag[p.f], p.WL, p.GL, p.WR, p.GR, p.dtf, a.ph, Fg, Wg, alpha, a.err, p.f);
   const int64_t ngp = a.ngp;
-#pragma unroll
-  for (int q = 0; q < 5; ++q) {
-    a.gpF[q * ngp + g] = Fg[q];
-    a.gpW[q * ngp + g] = Wg[q];
-  }
-  a.gpa[g] = alpha;
+  // one contiguous record per point, so that the gather reads a face's points as one segment
+  double2* dst = reinterpret_cast<double2*>(a.gpr + (int64_t)CGKS_GPR * g);
+  dst[0] = make_double2(Fg[0], Fg[1]);
+  dst[1] = make_double2(Fg[2], Fg[3]);
+  dst[2] = make_double2(Fg[4], Wg[0]);
+  dst[3] = make_double2(Wg[1], Wg[2]);
+  dst[4] = make_double2(Wg[3], Wg[4]);
+  dst[5] = make_double2(a.gp_A[g], a.gp_A[ngp + g]);
+  dst[6] = make_double2(a.gp_A[2 * ngp + g], alpha);
 }
 
 // forward-mode linearisation of one Gauss point: Jp[(10 k + o) ngp + g] = d out_o / d in_k with
@@ -748,52 +753,96 @@ struct GatherArgs {
   int64_t nc, ngp;
   const int8_t *ctype, *cside;
   const int32_t *cf, *gp_ptr;
-  const double *gp_A, *gpF, *gpW, *gpa, *vol, *dt, *W_in;
+  const double *gpr, *vol, *dt, *W_in;
   double *W_out, *res, *G_out, *alpha_out;
   int update;
   double gamma;
   DevErr* err;
 };
 
-HD void gather_body(int64_t i, const GatherArgs& a) {
-  const int64_t nc = a.nc, ngp = a.ngp;
-  double r[5] = {0, 0, 0, 0, 0}, gs[15];
+// running sums of one cell: residual, Gauss-Green gradient sums, compression-factor product
+struct GatherAcc {
+  double r[5], gs[15], al;
+};
+
+HD void gather_init(GatherAcc& c) {
 #pragma unroll
-  for (int j = 0; j < 15; ++j) gs[j] = 0.0;
-  double al = 1.0;
-  const int nt = a.ctype[i] == 7 ? 5 : a.ctype[i];  // faces: pyramids (type 7) have 5
-  for (int m = 0; m < nt; ++m) {
-    const int64_t f = a.cf[(int64_t)m * nc + i];
-    const double s = a.cside[(int64_t)m * nc + i] ? -1.0 : 1.0;
-    for (int64_t g = a.gp_ptr[f]; g < a.gp_ptr[f + 1]; ++g) {
-      const double A[3] = {s * a.gp_A[g], s * a.gp_A[ngp + g], s * a.gp_A[2 * ngp + g]};
+  for (int q = 0; q < 5; ++q) c.r[q] = 0.0;
 #pragma unroll
-      for (int q = 0; q < 5; ++q) {
-        r[q] -= s * a.gpF[q * ngp + g];
-        const double wq = a.gpW[q * ngp + g];
+  for (int j = 0; j < 15; ++j) c.gs[j] = 0.0;
+  c.al = 1.0;
+}
+
+// x with its sign bit xor-ed with `mask` (0 or the sign bit): an exact change of sign done by an
+// integer operation, so that it takes no FP64 issue slot (those bound the gather on GB300)
+HD double xor_sign(double x, uint64_t mask) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double(__double_as_longlong(x) ^ (long long)mask);
+#else
+  uint64_t u;
+  memcpy(&u, &x, sizeof u);
+  u ^= mask;
+  memcpy(&x, &u, sizeof x);
+  return x;
+#endif
+}
+
+// adds the ng consecutive Gauss-point records `rec` of one face, seen from its left cell (right:
+// false) or from its right cell (the flux and the area vector change sign), in ascending point order
+HD void gather_face(const double* rec, int ng, bool right, GatherAcc& c) {
+  const uint64_t m = right ? 0x8000000000000000ull : 0ull;
+  for (int k = 0; k < ng; ++k) {
+    const double* v = rec + (int64_t)CGKS_GPR * k;
+    const double A[3] = {xor_sign(v[10], m), xor_sign(v[11], m), xor_sign(v[12], m)};
 #pragma unroll
-        for (int d = 0; d < 3; ++d) gs[3 * q + d] += wq * A[d];
-      }
-      al *= a.gpa[g];
+    for (int q = 0; q < 5; ++q) {
+      c.r[q] -= xor_sign(v[q], m);
+      const double wq = v[5 + q];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) c.gs[3 * q + d] += wq * A[d];
     }
+    c.al *= v[13];
   }
+}
+
+// the cell's outputs from its sums: residual, alpha x Gauss-Green gradient / |Omega|, alpha, and
+// the optional explicit update W += dt/|Omega| Res
+HD void gather_store(int64_t i, const GatherArgs& a, const GatherAcc& c) {
+  const int64_t nc = a.nc;
   const double rv = 1.0 / a.vol[i];
   if (a.res)
 #pragma unroll
-    for (int q = 0; q < 5; ++q) a.res[q * nc + i] = r[q];
-  if (a.G_out)
+    for (int q = 0; q < 5; ++q) a.res[q * nc + i] = c.r[q];
+  if (a.G_out) {
+    const double k = c.al * rv;
 #pragma unroll
-    for (int j = 0; j < 15; ++j) a.G_out[j * nc + i] = al * gs[j] * rv;
-  if (a.alpha_out) a.alpha_out[i] = al;
+    for (int j = 0; j < 15; ++j) a.G_out[j * nc + i] = k * c.gs[j];
+  }
+  if (a.alpha_out) a.alpha_out[i] = c.al;
   if (a.update) {
     const double h = a.dt[i] * rv;
     double w[5];
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
-      w[q] = a.W_in[q * nc + i] + h * r[q];
+      w[q] = a.W_in[q * nc + i] + h * c.r[q];
       a.W_out[q * nc + i] = w[q];
     }
     const double p = (a.gamma - 1.0) * (w[4] - 0.5 * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]) / w[0]);
     if (!(w[0] > 0.0) || !(p > 0.0) || !isfinite(p)) set_err(a.err, CGKS_ENAN, (int)i, 6);
   }
+}
+
+// the gather of cell i, one face after the other in local-face order (the reference order: the
+// device kernel stages the same records through shared memory and sums them in the same order)
+HD void gather_body(int64_t i, const GatherArgs& a) {
+  const int64_t nc = a.nc;
+  GatherAcc c;
+  gather_init(c);
+  const int nt = a.ctype[i] == 7 ? 5 : a.ctype[i];  // faces: pyramids (type 7) have 5
+  for (int m = 0; m < nt; ++m) {
+    const int64_t f = a.cf[(int64_t)m * nc + i];
+    const int64_t g0 = a.gp_ptr[f];
+    gather_face(a.gpr + (int64_t)CGKS_GPR * g0, (int)(a.gp_ptr[f + 1] - g0), a.cside[(int64_t)m * nc + i] != 0, c);
+  }
+  gather_store(i, a, c);
 }

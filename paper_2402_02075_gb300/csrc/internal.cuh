@@ -12,6 +12,7 @@
 #define CGKS_MAXNF 6          // faces of a hexahedron
 #define CGKS_KOP 216          // reconstruction operator entries per cell: 9 x (4 * 6)
 #define CGKS_RC 50            // reconstruction coefficients per cell: 5 variables x 10
+#define CGKS_GPR 14           // Gauss-point record: flux x weight (5), interface state (5), area vector (3), alpha
 #define CGKS_AUX 8            // per-cell constants of the smoothness indicators
 #define CGKS_AGG_CAP 256      // records per coarse cell while building coarse faces
 #define HD __host__ __device__ __forceinline__
@@ -81,6 +82,28 @@ struct CoarseBuf {  // per coarse level work arrays
   double *lam = nullptr, *Dg = nullptr, *dU = nullptr;
 };
 
+// kernel kinds timed by cgks_profile (ids of cgks_kernel_stats)
+enum ProfKind {
+  PK_POINTS = 0,   // k_gks_points: Gauss points
+  PK_RECON,        // k_reconstruct: cells
+  PK_GATHER,       // k_gather: cells
+  PK_KFVS_FACES,   // k_kfvs_faces: faces of a coarse level
+  PK_KFVS_GATHER,  // k_kfvs_gather (FP64 and FP32 face fluxes): cells
+  PK_COARSE_DT,    // k_coarse_dt: cells
+  PK_FORCING,      // k_forcing: cells
+  PK_FE_UPDATE,    // k_fe_update: cells
+  PK_RESTRICT,     // k_restrict: cells of the finer level
+  PK_PROLONG,      // k_prolong / k_prolong_smooth: cells of the finer level
+  PK_KFVS_JVP,     // k_kfvs_jvp_faces: faces
+  PK_NORM,         // k_norm_partial + k_norm_final: cells
+  PK_COUNT
+};
+
+struct ProfRec {
+  cudaEvent_t e0, e1;
+  double units, bytes;
+};
+
 struct cgks_ctx {
   cgks_params P{};
   cudaStream_t stream = nullptr;
@@ -94,7 +117,7 @@ struct cgks_ctx {
   // fine state and work arrays
   double *W = nullptr, *G = nullptr, *alpha = nullptr;
   double *rc = nullptr, *dt = nullptr, *res = nullptr;
-  double *gpF = nullptr, *gpW = nullptr, *gpa = nullptr;
+  double* gpr = nullptr;            // [ngp][CGKS_GPR] Gauss-point records (112 bytes, 16-byte aligned)
   double *W1 = nullptr;             // copy of W used by the V-cycle
   double *ffl = nullptr;            // first-order face fluxes of level 0
   float* ffl32 = nullptr;           // their FP32 directional derivatives
@@ -109,6 +132,8 @@ struct cgks_ctx {
   // adjoint: the stored linearisation at the state of the last cgks_linearize, its time steps,
   // and the work arrays of the transposed products (in mesh_allocs)
   double *Jp = nullptr, *Jr = nullptr, *adt = nullptr;
+  double* aWG = nullptr;       // [21][nc] (W, grad W, alpha) at cgks_linearize (adjoint_recompute 1)
+  bool lin_recompute = false;  // the last cgks_linearize stored no reconstruction linearisation
   double *pbar = nullptr, *aself = nullptr, *arec = nullptr, *avec = nullptr, *apart = nullptr, *akry = nullptr;
   double* ajc = nullptr;  // per-cell shares of the wall force
   double* acb = nullptr;  // per-cell coefficient cotangents of a transposed product
@@ -120,18 +145,21 @@ struct cgks_ctx {
   std::vector<int32_t> h_cnodes, h_bnodes, h_btag, h_pairs;
   std::vector<void*> mesh_allocs;   // freed on re-upload / destroy
   std::vector<void*> ctx_allocs;    // freed on destroy
-  // kernel timing (cgks_profile): event pairs per fine kernel kind
+  // kernel timing (cgks_profile): event pairs per kernel kind, with the units and the algorithmic
+  // bytes of each recorded launch
   bool prof = false;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[3];
+  std::vector<ProfRec> prof_ev[PK_COUNT];
   std::vector<cudaEvent_t> ev_pool;
 };
 
-// event pair recorded around one launch of fine kernel kind k when profiling is enabled
+// event pair recorded around one launch of kernel kind k when profiling is enabled; units are the
+// cells, faces or Gauss points the launch processes, bytes its compulsory DRAM traffic (every input
+// read once, every output written once)
 struct ProfScope {
   cgks_ctx* c;
   int k;
   cudaEvent_t e1 = nullptr;
-  ProfScope(cgks_ctx* ctx, int kind);
+  ProfScope(cgks_ctx* ctx, int kind, double units, double bytes);
   ~ProfScope();
 };
 

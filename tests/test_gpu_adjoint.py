@@ -185,16 +185,43 @@ def test_adjoint_gradients_match_converged_differences(cg, ramp):
     assert abs(g["dJ_dmodes"][0] - fd_0) <= 1e-5 * abs(fd_0), (g["dJ_dmodes"][0], fd_0)
 
 
-def test_autograd_function_gives_the_adjoint_gradient(cg, ramp):
-    ctx, mesh, prm, W, G, modes, ref = ramp
-    f = cg.wall_force_function(ctx, modes[:2], tol=1e-11)
+def test_autograd_function_is_the_steady_wall_force_and_its_adjoint(cg, ramp):
+    """f(mach, amps) solves the steady problem at that Mach number on the mesh moved by the mode
+    amplitudes: at the fixture's steady state it returns its wall force and the adjoint gradient;
+    away from it (Mach 3.02, two modes displaced) it returns the wall force of a fresh solve on the
+    moved mesh, and its gradient matches central differences of f itself."""
+    ctx0, mesh, prm, W, G, modes, ref = ramp
+    ctx = cg.upload_mesh(mesh, cg.default_params(**prm))
+    ctx.state_init(_t(W), _t(G), _t(np.ones(ctx.nc)))
+    f = cg.wall_force_function(ctx, mesh, modes[:2], tol=1e-11)
     mach = torch.tensor(3.0, dtype=torch.float64, requires_grad=True)
     amps = torch.zeros(2, dtype=torch.float64, requires_grad=True)
     J = f(mach, amps)
     J.backward()
-    assert abs(float(J.detach()) - ctx.wall_force(1)) == 0.0
+    J0 = ctx0.wall_force(1)
+    assert abs(float(J.detach()) - J0) <= 1e-12 * abs(J0)
     assert abs(float(mach.grad) - ref["dJ_dmach"]) <= 1e-6 * abs(ref["dJ_dmach"])
     np.testing.assert_allclose(amps.grad.numpy(), ref["dJ_dmodes"], rtol=1e-6)
+    a1 = np.array([1e-3, -5e-4])
+    m1 = torch.tensor(3.02, dtype=torch.float64, requires_grad=True)
+    t1 = torch.tensor(a1, dtype=torch.float64, requires_grad=True)
+    J1 = f(m1, t1)
+    J1.backward()
+    moved = mg.displaced(mesh, a1[0] * modes[0] + a1[1] * modes[1], 1.0)
+    c = cg.upload_mesh(moved, cg.default_params(**dict(prm, mach=3.02)))
+    c.state_init(_t(W), _t(G), _t(np.ones(c.nc)))
+    _converge(c)
+    Jref = c.wall_force(1)
+    c.close()
+    assert abs(float(J1.detach()) - Jref) <= 1e-10 * abs(Jref), (float(J1), Jref)
+    h = 1e-6
+    with torch.no_grad():
+        fd_m = (float(f(m1 + h, t1)) - float(f(m1 - h, t1))) / (2 * h)
+        e0 = torch.tensor([h, 0.0], dtype=torch.float64)
+        fd_a = (float(f(m1, t1 + e0)) - float(f(m1, t1 - e0))) / (2 * h)
+    assert abs(float(m1.grad) - fd_m) <= 1e-5 * abs(fd_m), (float(m1.grad), fd_m)
+    assert abs(float(t1.grad[0]) - fd_a) <= 1e-5 * abs(fd_a), (float(t1.grad[0]), fd_a)
+    ctx.close()
 
 
 def test_larger_ramp_mach_gradient_matches_converged_differences(cg):
@@ -230,6 +257,44 @@ def test_gmres_and_pseudo_time_give_the_same_adjoint(ramp):
     # (lambda itself is not compared with the oracle's: at the steady state the linearisation has
     # entries at near-ties of |U.n| where one-sided derivatives and the oracle's central differences
     # differ; those directions do not reach the parameter gradients, which agree to 1e-6)
+
+
+@pytest.mark.parametrize("name", list(MESHES))
+def test_recomputed_product_equals_the_stored_one(cg, name):
+    """adjoint_recompute 1 keeps no linearisation of the reconstruction and recomputes its transposed
+    product (reverse mode through each cell's WENO reconstruction) in every product: J^T w agrees with
+    the product through the stored linearisation to round-off, on every mesh kind and boundary kind."""
+    mk, prm, amp = MESHES[name]
+    mesh = mk()
+    prm = dict(prm, n_levels=1, compression_factor=0)
+    ctx = cg.upload_mesh(mesh, cg.default_params(**prm))
+    nc = ctx.nc
+    rng = np.random.default_rng(17)
+    W, G = mg.uniform_state(nc, mach=prm["mach"])
+    W = W * (1.0 + amp * rng.standard_normal(W.shape))
+    G = 2.5 * amp * rng.standard_normal(G.shape)
+    ctx.state_init(_t(W), _t(G), _t(np.ones(nc)))
+    rb, gb = _t(rng.standard_normal((5, nc))), _t(rng.standard_normal((15, nc)))
+    outs = []
+    for rec in (0, 1):
+        ctx.set_params(cg.default_params(adjoint_recompute=rec, **prm))
+        ctx.linearize()
+        Wb, Gb = ctx.residual_vjp(rb, gb)
+        outs.append(np.concatenate([Wb.cpu().numpy().ravel(), Gb.cpu().numpy().ravel()]))
+    assert_normwise(outs[1][None], outs[0][None], 1e-12, "recomputed vs stored J^T w")
+    ctx.close()
+
+
+def test_recomputed_adjoint_gradients_match_dense_oracle_adjoint(cg, ramp):
+    """The whole gradient through the recomputed products agrees with the oracle's dense adjoint."""
+    ctx0, mesh, prm, W, G, modes, ref = ramp
+    ctx = cg.upload_mesh(mesh, cg.default_params(adjoint_recompute=1, **prm))
+    ctx.state_init(_t(W), _t(G), _t(np.ones(ctx.nc)))
+    g = ctx.adjoint(1, modes[:2], tol=1e-11)
+    assert g["rel_res"] <= 1e-11
+    assert abs(g["dJ_dmach"] - ref["dJ_dmach"]) <= 1e-6 * abs(ref["dJ_dmach"]), (g["dJ_dmach"], ref["dJ_dmach"])
+    np.testing.assert_allclose(g["dJ_dmodes"], ref["dJ_dmodes"], rtol=1e-6)
+    ctx.close()
 
 
 def test_reupload_into_the_same_context(cg):

@@ -1,0 +1,65 @@
+"""Converged steady states of the CUDA library against the oracle's own steady states.
+
+The oracle's states are stored in tests/golden/steady_*.npz by tests/golden/make_steady_states.py
+(oracle only, from the free stream, to a 1e-12 density-residual drop).  Here the library starts from
+the same free stream and iterates with its FP64 single grid, its FP64 V-cycle and its mixed-precision
+V-cycle (FP32 linearised coarse levels) to the same drop; every final state must agree with the
+oracle's within 1e-7 of each variable's largest magnitude (the momentum components sharing one
+scale), the bound the mixed-precision defect correction is held to.  Cases: Mach 3 compression
+ramps (shock from the corner, compression factor active there), compared with the oracle's single
+grid, and a laminar boundary layer with the extrapolation outflow, whose nonlinear WENO weights
+admit more than one steady state near the leading-edge corner, so that each iteration is compared
+with the same iteration of the oracle."""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+import meshgen as mg
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+sys.path.insert(0, GOLDEN)
+import make_steady_states as golden  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def cg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2402_02075_gb300 as cg
+    from paper_2402_02075_gb300 import build
+    build.build()
+    return cg
+
+
+def state_error(W, Wref):
+    """max |W - Wref| over each variable's largest |Wref| (momentum components share one scale)"""
+    s = np.abs(Wref).max(axis=1)
+    s[1:4] = s[1:4].max()
+    return float((np.abs(W - Wref).max(axis=1) / s).max())
+
+
+RUNS = [("single_grid_fp64", False, 0, "sg"), ("vcycle_fp64", True, 0, "vc"), ("vcycle_mixed", True, 1, "vc")]
+
+
+@pytest.mark.parametrize("name", list(golden.CASES))
+@pytest.mark.parametrize("run", RUNS, ids=[r[0] for r in RUNS])
+def test_steady_state_matches_the_oracle(cg, name, run):
+    key, multigrid, precision, it = run
+    ref = np.load(golden.reference(name, it))
+    mesh = golden.case_mesh(name)
+    ctx = cg.upload_mesh(mesh, cg.default_params(precision=precision, **golden.case_params(name)))
+    W, G = mg.uniform_state(ctx.nc, mach=golden.CASES[name][1]["mach"])
+    ctx.state_init(torch.from_numpy(W).cuda(), torch.from_numpy(G).cuda())
+    limit = 200000 if not multigrid else 60000
+    r = ctx.steady_solve(multigrid=multigrid, drop=1e-12, max_iters=limit, raise_on_notconv=False)
+    Wg = ctx.state_get()[0].cpu().numpy()
+    ctx.close()
+    err = state_error(Wg, ref["W"])
+    assert r["drop"] <= 1e-10, (key, r)
+    assert err <= 1e-7, (key, name, err, r)

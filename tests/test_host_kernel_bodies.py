@@ -101,7 +101,7 @@ extern "C" int host_fine(int64_t nc, int64_t nf, int64_t ngp, const int8_t* ctyp
                          const double* vol, const double* ctr, const double* m2, const double* Sn, const double* area,
                          const double* fshift, const double* fctr, const double* fnrm, const double* W, const double* G,
                          const double* alpha, const double* p, int cf_on, double* res, double* Gout, double* aout,
-                         const double* rbar, const double* gbar, double* out) {
+                         const double* rbar, const double* gbar, double* out, int recompute) {
   std::vector<double> Kop(216 * nc), ggw(18 * nc), lsw(18 * nc), aux(8 * nc), dtw(24 * nc);
   DevErr err{};
   ROArgs ro{nc, nf, ctype, cf, cside, fL, fR, vol, ctr, m2, Sn, area, fshift, fctr, fnrm,
@@ -120,20 +120,21 @@ extern "C" int host_fine(int64_t nc, int64_t nf, int64_t ngp, const int8_t* ctyp
   ph.viscous = p[1] > 0.0;
   ph.cf = cf_on;
   for (int q = 0; q < 5; ++q) ph.Winf[q] = p[5 + q];
-  std::vector<double> rc(50 * nc + 2), dt(nc), gpF(5 * ngp), gpW(5 * ngp), gpa(ngp);
+  std::vector<double> rc(50 * nc + 2), dt(nc), gpr(CGKS_GPR * ngp + 2);
   double* rca = rc.data() + ((reinterpret_cast<uintptr_t>(rc.data()) & 15) ? 1 : 0);  // 16-byte aligned
   ReconArgs ra{nc, nf, ctype, cf, fL, fR, ftag, cside, fnrm, Kop.data(), ggw.data(), lsw.data(), aux.data(),
                dtw.data(), vol, W, G, alpha, rca, dt.data(), ph, &err};
   for (int64_t i = 0; i < nc; ++i) reconstruct_body(i, ra);
-  PointArgs pa{ngp, nf, nc, gp_face, fL, fR, ftag, gp_x, gp_A, fshift, ctr, rca, dt.data(), gpF.data(), gpW.data(),
-               gpa.data(), ph, &err};
+  double* gpra = gpr.data() + ((reinterpret_cast<uintptr_t>(gpr.data()) & 15) ? 1 : 0);  // 16-byte aligned
+  PointArgs pa{ngp, nf, nc, gp_face, fL, fR, ftag, gp_x, gp_A, fshift, ctr, rca, dt.data(), gpra, ph, &err};
   for (int64_t g = 0; g < ngp; ++g) gks_point_body(g, pa);
-  GatherArgs ga{nc, ngp, ctype, cside, cf, gp_ptr, gp_A, gpF.data(), gpW.data(), gpa.data(), vol, dt.data(), W,
+  GatherArgs ga{nc, ngp, ctype, cside, cf, gp_ptr, gpra, vol, dt.data(), W,
                 nullptr, res, Gout, aout, 0, ph.gamma, &err};
   for (int64_t i = 0; i < nc; ++i) gather_body(i, ga);
   if (err.code || !rbar) return err.code;
-  std::vector<double> Jr((size_t)CGKS_RJ_ROWS * nc), Jp((size_t)CGKS_PJ_IN * CGKS_PJ_OUT * ngp);
-  for (int64_t i = 0; i < nc; ++i) recon_jacobian_body(i, ra, Jr.data());
+  std::vector<double> Jr(recompute ? 1 : (size_t)CGKS_RJ_ROWS * nc), Jp((size_t)CGKS_PJ_IN * CGKS_PJ_OUT * ngp);
+  if (!recompute)
+    for (int64_t i = 0; i < nc; ++i) recon_jacobian_body(i, ra, Jr.data());
   for (int64_t g = 0; g < ngp; ++g) point_jacobian_body(g, pa, Jp.data());
   std::vector<double> pbar(CGKS_PB * ngp + 2), self(20 * nc), rec(40 * nf + 2), cbuf(CGKS_RJ_OUT * nc);
   double* pb = pbar.data() + ((reinterpret_cast<uintptr_t>(pbar.data()) & 15) ? 1 : 0);
@@ -142,8 +143,12 @@ extern "C" int host_fine(int64_t nc, int64_t nf, int64_t ngp, const int8_t* ctyp
              Jp.data(), Jr.data(), rbar, gbar, pb, self.data(), rr, cbuf.data(), out};
   for (int64_t g = 0; g < ngp; ++g) vjp_point_body(g, va);
   for (int64_t i = 0; i < nc; ++i) vjp_coef_body(i, va);
-  for (int64_t i = 0; i < nc; ++i)
-    for (int k = 0; k < 50; ++k) vjp_slot_body(i, k, va, cbuf.data() + i, (int)nc);
+  if (recompute) {
+    for (int64_t i = 0; i < nc; ++i) vjp_recon_body(i, ra, va, cbuf.data() + i, nc);
+  } else {
+    for (int64_t i = 0; i < nc; ++i)
+      for (int k = 0; k < 50; ++k) vjp_slot_body(i, k, va, cbuf.data() + i, (int)nc);
+  }
   for (int64_t i = 0; i < nc; ++i) vjp_cell_body(i, va);
   return err.code;
 }
@@ -189,7 +194,7 @@ def host(tmp_path_factory):
     L.host_ghost.argtypes = [C.c_int, C.c_double] + [d_] * 6
     L.host_kfvs_jvp32.argtypes = [C.c_double] + [d_] * 6
     L.host_reconstruct.argtypes = [C.c_int64, C.c_int64] + [d_] * 20
-    L.host_fine.argtypes = [C.c_int64] * 3 + [d_] * 22 + [C.c_int] + [d_] * 6
+    L.host_fine.argtypes = [C.c_int64] * 3 + [d_] * 22 + [C.c_int] + [d_] * 6 + [C.c_int]
     return L
 
 
@@ -426,7 +431,7 @@ def test_fine_residual_on_the_host_matches_the_oracle(orc, host, name, cf_on):
     alpha = 1.0 - 0.1 * rng.random(nc)
     res, Gout, aout = np.zeros((5, nc)), np.zeros((15, nc)), np.zeros(nc)
     code = host.host_fine(nc, nf, ngp, *arrays, _p(W), _p(G), _p(alpha), _p(_phys_vector(prm)), cf_on, _p(res),
-                          _p(Gout), _p(aout), None, None, None)
+                          _p(Gout), _p(aout), None, None, None, 0)
     assert code == 0
     os_ = orc.Solver(om, orc.params(n_levels=1, compression_factor=cf_on, **prm))
     os_.set_state(W, G, alpha)
@@ -440,7 +445,9 @@ def test_fine_residual_on_the_host_matches_the_oracle(orc, host, name, cf_on):
 def test_adjoint_product_on_the_host_matches_oracle_differences(orc, host, name):
     """The adjoint's whole transposed product (forward-mode Jacobians of the reconstruction and the
     point flux, then the four transposed-product bodies), run on the host: w . (J v) = (J^T w) . v
-    with J v a Richardson-extrapolated central difference of the oracle's (Res, Gnew)."""
+    with J v a Richardson-extrapolated central difference of the oracle's (Res, Gnew).  Both ways of
+    taking the reconstruction's part: from its stored forward-mode linearisation, and recomputed by
+    the reverse-mode body (adjoint_recompute 1); the two products agree to round-off."""
     import meshgen as mg
     mk, prm = FINE_CASES[name]
     mesh = mk(mg)
@@ -459,15 +466,21 @@ def test_adjoint_product_on_the_host_matches_oracle_differences(orc, host, name)
     for _ in range(2):
         v = scale * rng.standard_normal(u.size)
         w = rng.standard_normal(u.size)
-        out = np.zeros((20, nc))
-        res, Gout, aout = np.zeros((5, nc)), np.zeros((15, nc)), np.zeros(nc)
-        code = host.host_fine(nc, nf, ngp, *arrays, _p(W), _p(G), _p(ones), _p(_phys_vector(prm)), 0, _p(res), _p(Gout),
-                              _p(aout), _p(w[:5 * nc]), _p(w[5 * nc:]), _p(out))
-        assert code == 0
+        outs = []
+        for recompute in (0, 1):
+            out = np.zeros((20, nc))
+            res, Gout, aout = np.zeros((5, nc)), np.zeros((15, nc)), np.zeros(nc)
+            code = host.host_fine(nc, nf, ngp, *arrays, _p(W), _p(G), _p(ones), _p(_phys_vector(prm)), 0, _p(res),
+                                  _p(Gout), _p(aout), _p(w[:5 * nc]), _p(w[5 * nc:]), _p(out), recompute)
+            assert code == 0
+            outs.append(out)
+        from parity import assert_normwise
+        assert_normwise(outs[1].ravel()[None], outs[0].ravel()[None], 1e-12, "recomputed vs stored J^T w")
 
         def jv(h):
             return (Fo(u + h * v) - Fo(u - h * v)) / (2 * h)
 
         Jv = (4.0 * jv(0.5e-7) - jv(1e-7)) / 3.0
-        lhs, rhs = float(w @ Jv), float(out.ravel() @ v)
-        assert abs(lhs - rhs) <= 1e-6 * float(np.abs(w) @ np.abs(Jv)), (name, lhs, rhs)
+        for out in outs:
+            lhs, rhs = float(w @ Jv), float(out.ravel() @ v)
+            assert abs(lhs - rhs) <= 1e-6 * float(np.abs(w) @ np.abs(Jv)), (name, lhs, rhs)
