@@ -47,15 +47,20 @@ SAMPLE = dict(nx=96, ny=4, nz=69, outflow=5)
 # FP64 floating-point operations per Gauss point of the gas-kinetic flux kernel (2 per DFMA, 1 per
 # DADD/DMUL), from the ncu instruction counts of a full capture of the kernel on the 48x32x32 box;
 # the kernel's own arithmetic, all of which the method needs
-FLOP_PER_GP = 3422.8
+FLOP_PER_GP = 3407.3
 # DRAM bytes (read + write) per Gauss point of the same kernel from the same capture (None when the
 # kernel has changed since)
-DRAM_BYTES_PER_GP = None
-# FP64 operations per cell of the reconstruction kernel, from the ncu instruction counts of a full
-# capture on the same box (DFMA 1,236.5, DMUL 542.9, DADD 356.3 per cell)
-FLOP_PER_CELL_RECON = 3372.2
-# kernels bound by the FP64 pipe (the rest are bound by HBM bandwidth): FLOP per unit
-ALU_KERNELS = {"k_gks_points": FLOP_PER_GP, "k_reconstruct": FLOP_PER_CELL_RECON}
+DRAM_BYTES_PER_GP = 173.7
+# FP64 operations per unit of the other kernels bound by the FP64 pipe, from ncu instruction counts
+# on the same box (2 per DFMA, 1 per DMUL or DADD; averages over the launches of a V-cycle):
+# reconstruction per cell (DFMA 1,243.4, DMUL 543.6, DADD 355.6), gather per Gauss point seen from a
+# cell (DFMA 15.67, DMUL 1.58, DADD 5.06), coarse KFVS face flux per face (DFMA 290.8, DMUL 89.2,
+# DADD 21.8).  The coarse time step and KFVS gather are latency-bound gathers, reported against HBM.
+FLOP_PER_CELL_RECON = 3385.9
+FLOP_PER_GP_SIDE_GATHER = 37.97
+FLOP_PER_FACE_KFVS = 692.6
+ALU_KERNELS = {"k_gks_points": FLOP_PER_GP, "k_reconstruct": FLOP_PER_CELL_RECON,
+               "k_gather": FLOP_PER_GP_SIDE_GATHER, "k_kfvs_faces": FLOP_PER_FACE_KFVS}
 
 
 def workload_name(w):
@@ -241,6 +246,10 @@ def kernel_rooflines(stats, steps, fp64_peak, hbm_peak):
             ach = ALU_KERNELS[name] * units / (ms * 1e-3) / 1e12
             row.update(bound="alu", unit="TFLOP/s", achieved=ach, peak=fp64_peak,
                        frac=ach / fp64_peak if fp64_peak else None, flop_per_unit=ALU_KERNELS[name])
+            # the memory side of the same launches, for comparison
+            row["hbm_GBps"] = by / (ms * 1e-3) / 1e9
+            row["hbm_frac"] = row["hbm_GBps"] / hbm_peak if hbm_peak else None
+            row["algorithmic_bytes_per_launch"] = by / n
         else:
             ach = by / (ms * 1e-3) / 1e9
             row.update(bound="hbm", unit="GB/s", achieved=ach, peak=hbm_peak,

@@ -70,8 +70,8 @@ typedef struct {
                           the states, updates and correction stay FP64 */
   int32_t coarse_smoother; /* 0 forward Euler (Sec. 4.2); 1 LU-SGS, the implicit variant of Sec. 4.3 */
   int32_t compression_factor; /* 1 (default): the gradient compression factor of Sec. 3.3; 0: alpha = 1
-                                 (no compression), for shock-free flows: its |p_l - p_r| terms are not
-                                 smooth at zero and hold V-cycles at a residual floor near convergence */
+                                 (no compression), which the adjoint needs: the factor's |p_l - p_r|
+                                 terms have no derivative where the jump vanishes */
   int32_t prolongation;    /* 0 injection (Sec. 4.2); 1 injection smoothed once over face neighbours: a
                               cell receives the volume-weighted mean of its own and its neighbours'
                               injected corrections (not in the paper) */
@@ -255,7 +255,7 @@ cgks_status cgks_fp64_peak(double* tflops);
  * output written once; the per-unit formulas are those of the kernels' documentation).  Kernel ids
  * (`which`):
  *   0 Gauss-point gas-kinetic flux (units: Gauss points)   1 reconstruction (cells)
- *   2 fine gather / update (cells)                         3 coarse KFVS face fluxes (faces)
+ *   2 fine gather / update (Gauss points seen from cells)  3 coarse KFVS face fluxes (faces)
  *   4 coarse KFVS gather (cells)                           5 coarse local time step (cells)
  *   6 FAS forcing (cells)                                  7 coarse forward-Euler update (cells)
  *   8 restriction (cells of the finer level)               9 prolongation (cells of the finer level)

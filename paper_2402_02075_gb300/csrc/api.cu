@@ -367,6 +367,14 @@ cgks_status cgks_mesh_upload(cgks_ctx* ctx, int64_t n_nodes, const double* xyz, 
   ctx->h_pairs.assign(n_periodic ? periodic_pairs : nullptr, n_periodic ? periodic_pairs + 2 * n_periodic : nullptr);
   CKS(build_fine_mesh(ctx, n_nodes, xyz, n_cells, cell_type, cell_ptr, cell_nodes, n_bfaces,
                       n_bfaces ? bface_ptr : &empty64, bface_nodes, bface_tag, periodic_pairs, n_periodic));
+  {  // Gauss points seen from the cells: tet 4 x 3, prism 2 x 3 + 3 x 4, hex 6 x 4, pyramid 4 + 4 x 3
+    int64_t s = 0;
+    for (int64_t c = 0; c < n_cells; ++c) {
+      const int t = cell_type[c];
+      s += t == 4 ? 12 : t == 5 ? 18 : t == 6 ? 24 : 16;
+    }
+    ctx->F.gp_sides = s;
+  }
   CKS(build_levels(ctx));
   const Fine& F = ctx->F;
   auto& M = ctx->mesh_allocs;

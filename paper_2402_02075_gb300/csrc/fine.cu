@@ -152,7 +152,7 @@ cgks_status fine_gather(cgks_ctx* ctx, const double* W_in, double* W_out, double
                 ctx->dt, W_in, W_out, res, G_out, alpha_out, update, ctx->P.gamma, ctx->derr};
   {
     const double per_cell = 1 + 8 + (update ? 88 : 0) + (res ? 40 : 0) + (G_out ? 120 : 0) + (alpha_out ? 8 : 0);
-    ProfScope ps(ctx, PK_GATHER, (double)F.nc,
+    ProfScope ps(ctx, PK_GATHER, (double)F.gp_sides,
                  F.nc * per_cell + (F.nf + F.n_int + F.n_per) * 5.0 + F.nf * 4.0 + F.ngp * 8.0 * CGKS_GPR);
     static bool smem_set = false;  // the kernel's dynamic shared memory exceeds the 48 KiB default
     if (!smem_set) {

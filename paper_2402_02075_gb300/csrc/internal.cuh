@@ -56,6 +56,7 @@ struct Level {
 // the fine mesh with its Gauss points and reconstruction operators
 struct Fine {
   int64_t nc = 0, nf = 0, n_int = 0, n_per = 0, n_bnd = 0, ngp = 0;
+  int64_t gp_sides = 0;  // Gauss points summed over every cell's faces (interior points counted twice)
   int8_t* ctype = nullptr;
   double *vol = nullptr, *ctr = nullptr, *m2 = nullptr;          // [nc], [3][nc], [6][nc]
   int32_t *fL = nullptr, *fR = nullptr, *ftag = nullptr, *ftagR = nullptr, *flf = nullptr;

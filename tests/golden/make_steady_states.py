@@ -4,7 +4,7 @@ Calls only the CPU oracle (oracle/) on the seeded synthetic meshes of meshgen; n
 from the CUDA library.  Each case is iterated from the uniform free stream by the oracle's own
 single-grid steps or V-cycles (Sec. 4.2 of the paper) until the density-residual norm has fallen by
 `drop` relative to its first value, and stored as tests/golden/steady_<name>_<sg|vc>.npz with W [5][N],
-gradW [15][N], alpha [N], the iteration count and the final drop.  The ramps have one steady state,
+alpha [N], the iteration count and the final drop.  The ramps have one steady state,
 so their single-grid state serves every iteration; the boundary layer's nonlinear WENO weights admit
 more than one near the leading-edge corner, so it is stored for both iterations and each is compared
 with the same iteration of the library.
@@ -75,7 +75,7 @@ def make(name, chunk=200):
             if last <= drop:
                 break
         W, G, a = S.state()
-        np.savez_compressed(path(name, itn), W=W, G=G, alpha=a, iters=it, drop=last, multigrid=multigrid)
+        np.savez_compressed(path(name, itn), W=W, alpha=a, iters=it, drop=last, multigrid=multigrid)
         print(f"{name} {itn}: {M.nc} cells, {it} {'V-cycles' if multigrid else 'steps'}, drop {last:.2e}, "
               f"{time.time() - t0:.0f} s", flush=True)
 
