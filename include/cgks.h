@@ -175,7 +175,11 @@ cgks_status cgks_vcycle(cgks_ctx* ctx, int n_cycles, double* norm_hist);
 
 /* Iterates cgks_vcycle (multigrid != 0) or cgks_step until the residual norm falls below
  * drop x (first norm) or max_iters iterations.  Host outputs (nullable): iterations done, final
- * norm ratio, wall seconds.  The norm is read every `check_every` = 10 iterations.
+ * norm ratio, wall seconds.  The norm is read every `check_every` = 10 iterations.  After the first
+ * 10 iterations, which run eagerly, each further chunk of 10 replays one CUDA graph (the same
+ * kernels in the same order: the results are those of eager launches), on a private stream of the
+ * context ordered after and before the context stream by events; not while kernel timing
+ * (cgks_profile) is on.
  * CGKS_ENOTCONV when max_iters is reached first. */
 cgks_status cgks_steady_solve(cgks_ctx* ctx, int multigrid, double drop, int64_t max_iters, int64_t* iters_done,
                               double* final_drop, double* seconds);

@@ -312,6 +312,12 @@ cgks_status cgks_destroy(cgks_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   release_events(ctx);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  if (ctx->gstream) {
+    cudaStreamSynchronize(ctx->gstream);
+    cudaStreamDestroy(ctx->gstream);
+  }
+  for (cudaEvent_t e : ctx->gev)
+    if (e) cudaEventDestroy(e);
   free_list(ctx->mesh_allocs);
   free_list(ctx->ctx_allocs);
   if (ctx->h_err) cudaFreeHost(ctx->h_err);
@@ -549,6 +555,62 @@ cgks_status cgks_vcycle(cgks_ctx* ctx, int n_cycles, double* norm_hist) {
   return run_iterations(ctx, n_cycles, norm_hist, true, "cgks_vcycle");
 }
 
+// one chunk of n iterations (V-cycles or single-grid steps) enqueued eagerly, the density norm of
+// iteration k into hist[k]
+static cgks_status enqueue_chunk(cgks_ctx* ctx, bool multigrid, int n, double* hist) {
+  for (int k = 0; k < n; ++k) CKS(multigrid ? vcycle_once(ctx, hist + k) : step_once(ctx, hist + k));
+  return CGKS_OK;
+}
+
+// the same chunk captured once into a CUDA graph (the iterations are launch sequences of fixed shape,
+// so small meshes pay one graph launch instead of tens of kernel launches per iteration).  Capture
+// and replay run on a private non-blocking stream, ordered after and before the context stream by
+// events (the context stream may be the legacy default stream, which cannot be captured).
+static cgks_status graph_stream(cgks_ctx* ctx) {
+  if (!ctx->gstream) CK(cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking));
+  for (cudaEvent_t& e : ctx->gev)
+    if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  return CGKS_OK;
+}
+
+// false when capture is not possible; the caller then runs the chunk eagerly
+static bool capture_chunk(cgks_ctx* ctx, bool multigrid, int n, double* hist, cudaGraphExec_t* exec) {
+  if (graph_stream(ctx) != CGKS_OK) {
+    ctx->err.clear();
+    return false;
+  }
+  cudaStream_t user = ctx->stream, gs = ctx->gstream;
+  if (cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  ctx->stream = gs;
+  const cgks_status s = enqueue_chunk(ctx, multigrid, n, hist);
+  ctx->stream = user;
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(gs, &graph);
+  bool ok = s == CGKS_OK && e == cudaSuccess && graph;
+  if (ok) ok = cudaGraphInstantiate(exec, graph, 0) == cudaSuccess;
+  if (graph) cudaGraphDestroy(graph);
+  if (!ok) {
+    *exec = nullptr;
+    cudaGetLastError();
+    ctx->err.clear();
+  }
+  return ok;
+}
+
+// one replay of the captured chunk, after the work already queued on the context stream and before
+// whatever is queued on it next
+static cgks_status replay_chunk(cgks_ctx* ctx, cudaGraphExec_t exec) {
+  CK(cudaEventRecord(ctx->gev[0], ctx->stream));
+  CK(cudaStreamWaitEvent(ctx->gstream, ctx->gev[0], 0));
+  CK(cudaGraphLaunch(exec, ctx->gstream));
+  CK(cudaEventRecord(ctx->gev[1], ctx->gstream));
+  CK(cudaStreamWaitEvent(ctx->stream, ctx->gev[1], 0));
+  return CGKS_OK;
+}
+
 cgks_status cgks_steady_solve(cgks_ctx* ctx, int multigrid, double drop, int64_t max_iters, int64_t* iters_done,
                               double* final_drop, double* seconds) {
   NEED_STATE();
@@ -562,9 +624,18 @@ cgks_status cgks_steady_solve(cgks_ctx* ctx, int multigrid, double drop, int64_t
   double r0 = 0.0, ratio = 1.0;
   int64_t it = 0;
   cgks_status s = CGKS_OK;
+  // the first chunk runs eagerly (it builds whatever is built on first use); full chunks after it
+  // replay one captured graph, unless kernel timing is on (it records events around each launch)
+  cudaGraphExec_t exec = nullptr;
+  bool try_graph = !ctx->prof;
   while (it < max_iters && s == CGKS_OK) {
     const int n = (int)std::min<int64_t>(check_every, max_iters - it);
-    for (int k = 0; k < n && s == CGKS_OK; ++k) s = multigrid ? vcycle_once(ctx, hist + k) : step_once(ctx, hist + k);
+    if (it > 0 && n == check_every && try_graph && !exec) try_graph = capture_chunk(ctx, multigrid != 0, n, hist, &exec);
+    if (exec && n == check_every) {
+      s = replay_chunk(ctx, exec);
+    } else {
+      s = enqueue_chunk(ctx, multigrid != 0, n, hist);
+    }
     if (s != CGKS_OK) break;
     s = read_norm(ctx, hist, h.data(), n);
     if (s != CGKS_OK) break;
@@ -575,6 +646,7 @@ cgks_status cgks_steady_solve(cgks_ctx* ctx, int multigrid, double drop, int64_t
     ratio = r0 > 0.0 ? h[n - 1] / r0 : 0.0;
     if (ratio <= drop) break;
   }
+  if (exec) cudaGraphExecDestroy(exec);
   const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   free_list(tmp);
   CKS(s);

@@ -151,6 +151,9 @@ struct cgks_ctx {
   bool prof = false;
   std::vector<ProfRec> prof_ev[PK_COUNT];
   std::vector<cudaEvent_t> ev_pool;
+  // private non-blocking stream and ordering events of the graph-replayed steady-solve chunks
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t gev[2] = {nullptr, nullptr};
 };
 
 // event pair recorded around one launch of kernel kind k when profiling is enabled; units are the

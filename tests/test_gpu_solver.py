@@ -246,3 +246,31 @@ def test_vcycles_with_relaxed_or_smoothed_correction(cg, orc, extra):
     ho = os_.run(3, multigrid=True)
     np.testing.assert_allclose(hg, ho, rtol=1e-9)
     _compare_states(ctx, os_)
+
+
+@pytest.mark.parametrize("multigrid,extra", [(False, {}), (True, {}), (True, dict(precision=1)),
+                                             (True, dict(coarse_smoother=1))],
+                         ids=["single grid", "V-cycle", "mixed V-cycle", "LU-SGS V-cycle"])
+def test_graph_replayed_steady_solve_equals_eager_iterations(cg, multigrid, extra):
+    """cgks_steady_solve replays its chunks of 10 iterations as a captured CUDA graph after the first
+    chunk: 50 iterations of it leave bit for bit the state, gradients and compression factors of 50
+    eagerly launched iterations (cgks_step / cgks_vcycle), with the same residual norms."""
+    mesh = mg.wall_box(12, 4, 12, first=2e-3, ratio=1.3, outflow=mg.BC_SUPER_OUT)
+    prm = dict(mach=0.5, viscous=1, reynolds=1e4, prandtl=0.72, n_levels=3, **extra)
+    out = []
+    for graphs in (True, False):
+        ctx = cg.upload_mesh(mesh, cg.default_params(**prm))
+        W, G = mg.uniform_state(ctx.nc, mach=0.5)
+        ctx.state_init(_t(W), _t(G))
+        if graphs:
+            r = ctx.steady_solve(multigrid=multigrid, drop=1e-300, max_iters=50, raise_on_notconv=False)
+            assert r["iters"] == 50 and not r["converged"]
+            last = r["drop"]
+        else:
+            h = ctx.vcycle(50) if multigrid else ctx.step(50)
+            last = h[-1] / h[0]
+        out.append(([x.cpu().numpy() for x in ctx.state_get()], last))
+        ctx.close()
+    for a, b in zip(out[0][0], out[1][0]):
+        assert np.array_equal(a, b)
+    assert out[0][1] == out[1][1]

@@ -227,3 +227,24 @@ def test_vcycle_damps_a_smooth_perturbation_faster_than_the_single_grid(orc, ram
         errs[mgrid] = np.abs(T.state()[0] - W).max()
     e0 = np.abs(Wp - W).max()
     assert errs[True] < 0.5 * errs[False] < 0.5 * e0, (e0, errs)
+
+
+@pytest.mark.parametrize("mk", [lambda: mg.periodic_box(6), lambda: mg.scale_box(12), lambda: mg.pyramid_box(6)],
+                         ids=["jittered quadrant box", "jittered scale box", "pyramids"])
+def test_coarsening_volumes_equal_the_solver_volumes(orc, mk):
+    """The coarsening takes its own geometry of the fine level (node-mean centres, diagonal area
+    vectors, divergence-theorem volumes), so that merges are decided on the same bits in the oracle
+    and on the GPU.  Its volumes are the solver's Gauss-rule volumes to round-off on jittered mixed
+    cells (both formulas are exact for the trilinear cells), so the restriction weights, the coarse
+    volumes (sums of them) and the injected corrections conserve the solver's sum |Omega| W: the
+    V-cycle conservation test with one global time step holds to 1e-14 for that reason."""
+    M = orc.Mesh(mk())
+    V = M.cells()[0]
+    Vc = M.coarsening_geometry()[0]
+    assert np.abs(V - Vc).max() <= 1e-14 * V.max()
+    S = orc.Solver(M, orc.params(mach=0.3, n_levels=3))
+    for lev in (1, 2):
+        L, F = S.level(lev), S.level(lev - 1)
+        agg = np.zeros(L["nc"])
+        np.add.at(agg, L["map"], V if lev == 1 else F["vol"])
+        assert np.abs(agg - L["vol"]).max() <= 1e-13 * L["vol"].max()
