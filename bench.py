@@ -767,7 +767,7 @@ def main():
            "config": {"workload": workload_name(WORKLOAD), "cells_per_level": [l[0] for l in levels],
                       "faces_per_level": [l[1] for l in levels], "gauss_points": ngp,
                       "parallelism": "replicas" if world > 1 else "single GPU",
-                      "l2": "working set (~6 GB) far above L2 (129 MB); no flush needed",
+                      "l2": "working set (about 7 GB) far above L2 (129 MB); no flush needed",
                       "setup_s": setup_s, "params": {k: v for k, v in PARAMS.items()}},
            "e2e": e2e, "gpu_launches": launches * args.steps, "roofline": roofline, "clocks": clk.summary(),
            "mixed": mixed}

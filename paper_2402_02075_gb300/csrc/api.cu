@@ -287,6 +287,7 @@ cgks_status cgks_create(const cgks_params* params, void* cuda_stream, cgks_ctx**
   ctx->P = *params;
   ctx->stream = (cudaStream_t)cuda_stream;
   cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->device);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_err, sizeof(DevErr));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_count, sizeof(int64_t));
   if (e != cudaSuccess) {

@@ -290,8 +290,8 @@ cgks_status kfvs_residual(cgks_ctx* ctx, int lev, const double* W, double* res) 
   const double entries = (double)(L.nf + L.n_int + L.n_per);
   {
     ProfScope ps(ctx, PK_KFVS_FACES, (double)L.nf, L.nf * 76.0 + L.nc * 40.0);
-    k_kfvs_faces<<<grid_for(L.nf, 256), 256, 0, ctx->stream>>>(L.nf, L.fL, L.fR, L.ftag, L.Sn, L.nc, W, ff, ph,
-                                                                ctx->derr);
+    const int b = spread_block(L.nf, 256, ctx->n_sm);
+    k_kfvs_faces<<<grid_for(L.nf, b), b, 0, ctx->stream>>>(L.nf, L.fL, L.fR, L.ftag, L.Sn, L.nc, W, ff, ph, ctx->derr);
   }
   {
     ProfScope ps(ctx, PK_KFVS_GATHER, (double)L.nc, L.nc * 44.0 + entries * 4.0 + L.nf * 48.0);
@@ -325,8 +325,9 @@ cgks_status coarse_dt(cgks_ctx* ctx, int lev, const double* W, double* dt) {
   const Level& L = ctx->L[lev];
   {
     ProfScope ps(ctx, PK_COARSE_DT, (double)L.nc, L.nc * 60.0 + (L.nf + L.n_int + L.n_per) * 4.0 + L.nf * 32.0);
-    k_coarse_dt<<<grid_for(L.nc, 256), 256, 0, ctx->stream>>>(L.nc, L.nf, L.c2f_ptr, L.c2f, L.Sn, L.area, L.vol, W,
-                                                              dt, ctx->P.gamma, ctx->P.cfl_coarse);
+    const int b = spread_block(L.nc, 256, ctx->n_sm);
+    k_coarse_dt<<<grid_for(L.nc, b), b, 0, ctx->stream>>>(L.nc, L.nf, L.c2f_ptr, L.c2f, L.Sn, L.area, L.vol, W, dt,
+                                                          ctx->P.gamma, ctx->P.cfl_coarse);
   }
   if (ctx->P.dt_mode == 1) CKS(global_min_dt(ctx, dt, L.nc));
   CK(cudaGetLastError());

@@ -132,14 +132,16 @@ cgks_status fine_fluxes(cgks_ctx* ctx, const double* W, const double* G, const d
   const double slots = (double)(F.nf + F.n_int + F.n_per);
   {
     ProfScope ps(ctx, PK_RECON, (double)F.nc, F.nc * (306.0 * 8 + 1 + 51.0 * 8) + slots * 5 + F.nf * 36.0);
-    k_reconstruct<<<grid_for(F.nc, 128), 128, 0, ctx->stream>>>(ra);
+    const int b = spread_block(F.nc, 128, ctx->n_sm);
+    k_reconstruct<<<grid_for(F.nc, b), b, 0, ctx->stream>>>(ra);
   }
   if (ctx->P.dt_mode == 1) CKS(global_min_dt(ctx, ctx->dt, F.nc));
   PointArgs pa{F.ngp, F.nf, F.nc, F.gp_face, F.fL, F.fR, F.ftag, F.gp_x, F.gp_A, F.fshift, F.ctr, ctx->rc,
                ctx->dt, ctx->gpr, ph, ctx->derr};
   {
     ProfScope ps(ctx, PK_POINTS, (double)F.ngp, F.ngp * (52.0 + 8.0 * CGKS_GPR) + F.nf * 36.0 + F.nc * 432.0);
-    k_gks_points<<<grid_for(F.ngp, 128), 128, 0, ctx->stream>>>(pa);
+    const int b = spread_block(F.ngp, 128, ctx->n_sm);
+    k_gks_points<<<grid_for(F.ngp, b), b, 0, ctx->stream>>>(pa);
   }
   CK(cudaGetLastError());
   return CGKS_OK;

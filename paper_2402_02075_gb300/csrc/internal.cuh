@@ -109,6 +109,7 @@ struct cgks_ctx {
   cgks_params P{};
   cudaStream_t stream = nullptr;
   int device = 0;
+  int n_sm = 152;  // streaming multiprocessors of the device
   std::string err;
   bool has_mesh = false, has_state = false;
   Fine F;
@@ -189,6 +190,17 @@ cgks_status dalloc(cgks_ctx* ctx, std::vector<void*>& list, T** p, size_t count)
 void free_list(std::vector<void*>& list);
 
 inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
+
+// block size of a launch of n long FP64-bound threads: `max_block` when the launch fills every SM,
+// else smaller blocks (a multiple of the warp, at least one) so that the threads spread over all the
+// SMs: an SM issues 2 FP64 operations per clock, so a few blocks queued on a few SMs of a small
+// mesh would take as long as a full wave
+inline int spread_block(int64_t n, int max_block, int n_sm) {
+  const int64_t per_sm = (n + n_sm - 1) / n_sm;
+  if (per_sm >= max_block) return max_block;
+  const int64_t b = ((per_sm + 31) / 32) * 32;
+  return (int)(b < 32 ? 32 : b);
+}
 
 // exclusive prefix sum of n int32 values (device), total returned through *total (host) when
 // non-null (synchronises).  Uses ctx scratch allocated on demand.
