@@ -718,6 +718,20 @@ def main():
     e2e_s = max_over_ranks(time.perf_counter() - t0)
     e2e = {"value": job_rate(nc, args.steps, e2e_s * 1e3, world), "unit": UNIT,
            "h2d_bytes_per_step": int(Wh.numel() + Gh.numel() + ah.numel()) * 8, "d2h_bytes_per_step": 8}
+    # single-grid FP64 steps on the same workload: their rate, and a V-cycle's cost in steps
+    ctx.state_init(Wd, Gd)
+    ctx.step(args.warmup, history=False)
+    barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    ctx.step(args.steps, history=False)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_sg = max_over_ranks(ev0.elapsed_time(ev1))
+    single_grid = {"value": job_rate(nc, args.steps, ms_sg, world), "unit": UNIT, "ms_per_step": ms_sg / args.steps,
+                   "vcycle_cost_in_steps": ms_max / ms_sg,
+                   "what": "explicit single-grid FP64 CGKS steps (Eq. smo with local time steps)"}
     # the mixed-precision V-cycle on the same workload: coarse levels in FP32 defect-correction form
     ctx.set_params(cg.default_params(precision=1, **PARAMS))
     ctx.state_init(Wd, Gd)
@@ -770,7 +784,7 @@ def main():
                       "l2": "working set (about 7 GB) far above L2 (129 MB); no flush needed",
                       "setup_s": setup_s, "params": {k: v for k, v in PARAMS.items()}},
            "e2e": e2e, "gpu_launches": launches * args.steps, "roofline": roofline, "clocks": clk.summary(),
-           "mixed": mixed}
+           "mixed": mixed, "single_grid": single_grid}
     ctx.close()
     if rank == 0 and world == 1 and not args.no_ramp:
         out["ramp"] = run_ramp_throughput(cg, torch, args.steps, args.warmup)
