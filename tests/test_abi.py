@@ -43,6 +43,8 @@ def test_context_free_checks_need_no_device(lib):
     p = cg.Params()
     assert L.cgks_default_params(ctypes.byref(p)) == 0
     assert abs(p.gamma - 1.4) < 1e-15 and p.n_levels == 3 and p.pre == 1 and p.post == 0
+    assert p.compression_factor == 1 and p.adjoint_recompute == 0 and p.agglo_seed == 0
+    assert ctypes.sizeof(cg.Params) == 14 * 8 + 12 * 4 + 8  # the C struct: no padding, seed last
     assert L.cgks_default_params(None) == 1
     assert L.cgks_destroy(None) == 0
     assert L.cgks_density_norm_noalloc(None, None, 10, None, None) == 1
