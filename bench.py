@@ -53,14 +53,18 @@ FLOP_PER_GP = 3407.3
 DRAM_BYTES_PER_GP = 173.7
 # FP64 operations per unit of the other kernels bound by the FP64 pipe, from ncu instruction counts
 # on the same box (2 per DFMA, 1 per DMUL or DADD; averages over the launches of a V-cycle):
-# reconstruction per cell (DFMA 1,243.4, DMUL 543.6, DADD 355.6), gather per Gauss point seen from a
-# cell (DFMA 15.67, DMUL 1.58, DADD 5.06), coarse KFVS face flux per face (DFMA 290.8, DMUL 89.2,
-# DADD 21.8).  The coarse time step and KFVS gather are latency-bound gathers, reported against HBM.
+# reconstruction per cell (DFMA 1,243.4, DMUL 543.6, DADD 355.6), gather with the gradient update per
+# Gauss point seen from a cell (DFMA 16.06, DMUL 2.17, DADD 5.11), the flux alone of the V-cycle's
+# defect per Gauss point (DFMA 1,192.0, DMUL 623.5, DADD 250.0), coarse KFVS face flux per face (DFMA
+# 290.8, DMUL 89.2, DADD 21.8).  The residual-only gather of the defect (5.6 FLOP per point seen), the
+# coarse time step and the KFVS gather are latency-bound gathers, reported against HBM.
 FLOP_PER_CELL_RECON = 3385.9
-FLOP_PER_GP_SIDE_GATHER = 37.97
+FLOP_PER_GP_SIDE_GATHER = 39.39
+FLOP_PER_GP_FLUX = 3257.5
 FLOP_PER_FACE_KFVS = 692.6
 ALU_KERNELS = {"k_gks_points": FLOP_PER_GP, "k_reconstruct": FLOP_PER_CELL_RECON,
-               "k_gather": FLOP_PER_GP_SIDE_GATHER, "k_kfvs_faces": FLOP_PER_FACE_KFVS}
+               "k_gather": FLOP_PER_GP_SIDE_GATHER, "k_kfvs_faces": FLOP_PER_FACE_KFVS,
+               "k_gks_points_flux": FLOP_PER_GP_FLUX}
 
 
 def workload_name(w):

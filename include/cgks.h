@@ -264,9 +264,11 @@ cgks_status cgks_fp64_peak(double* tflops);
  *   6 FAS forcing (cells)                                  7 coarse forward-Euler update (cells)
  *   8 restriction (cells of the finer level)               9 prolongation (cells of the finer level)
  *  10 FP32 KFVS directional derivative (faces)            11 residual norm (cells)
+ *  12 Gauss-point flux alone, for the V-cycle's defect     13 fine gather of the residual alone
+ *     (Gauss points)                                          (Gauss points seen from cells)
  * cgks_kernel_stats synchronises the stream and returns (host outputs, each nullable) the summed
  * device time in milliseconds, the number of launches, the summed units and the summed algorithmic
- * bytes of kernel `which` recorded since profiling was enabled; an id outside 0..11 is CGKS_EINVAL. */
+ * bytes of kernel `which` recorded since profiling was enabled; an id outside 0..13 is CGKS_EINVAL. */
 cgks_status cgks_profile(cgks_ctx* ctx, int enable);
 cgks_status cgks_kernel_stats(cgks_ctx* ctx, int which, double* ms, int64_t* launches, double* units,
                               double* bytes);

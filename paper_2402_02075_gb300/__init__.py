@@ -258,7 +258,8 @@ class Context:
         _check(load().cgks_profile(self.h, int(bool(enable))), self.h)
 
     KERNELS = ("k_gks_points", "k_reconstruct", "k_gather", "k_kfvs_faces", "k_kfvs_gather", "k_coarse_dt",
-               "k_forcing", "k_fe_update", "k_restrict", "k_prolong", "k_kfvs_jvp_faces", "k_norm")
+               "k_forcing", "k_fe_update", "k_restrict", "k_prolong", "k_kfvs_jvp_faces", "k_norm",
+               "k_gks_points_flux", "k_gather_res")
 
     def kernel_stats(self, which):
         """(total device ms, launches, units, algorithmic bytes) of kernel `which` (an index or a name

@@ -419,8 +419,9 @@ cgks_status vcycle_once(cgks_ctx* ctx, double* norm_dev) {
   const Fine& F = ctx->F;
   const Level& C1 = ctx->L[1];
   CoarseBuf& B1 = ctx->C[1];
-  // defect at the smoothed state (gradient and compression outputs discarded)
-  CKS(fine_fluxes(ctx, ctx->W, ctx->G, ctx->alpha));
+  // defect at the smoothed state (the residual alone: no interface state, gradient or compression
+  // factor is formed)
+  CKS(fine_fluxes(ctx, ctx->W, ctx->G, ctx->alpha, false));
   CKS(fine_gather(ctx, ctx->W, nullptr, ctx->res, nullptr, nullptr, 0));
   {
     ProfScope ps(ctx, PK_RESTRICT, (double)F.nc, F.nc * 92.0 + C1.nc * 92.0);

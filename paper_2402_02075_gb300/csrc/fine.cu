@@ -1,14 +1,15 @@
 // Kernels of the fine-level CGKS residual (bodies in fine.cuh) and their host launchers.
 #include "fine.cuh"
 
-__global__ void __launch_bounds__(128) k_reconstruct(ReconArgs a) {
+__global__ void __launch_bounds__(128, 4) k_reconstruct(ReconArgs a) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < a.nc) reconstruct_body(i, a);
 }
 
+template <bool STATE>
 __global__ void __launch_bounds__(128) k_gks_points(PointArgs a) {
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (g < a.ngp) gks_point_body(g, a);
+  if (g < a.ngp) gks_point_body<STATE>(g, a);
 }
 
 // ---- gather: per cell, fixed-order sums of its faces' Gauss-point records ----------------------
@@ -18,7 +19,8 @@ __global__ void __launch_bounds__(128) k_gks_points(PointArgs a) {
 // with 16-byte cp.async copies, lanes of one copy instruction covering one face's contiguous bytes
 // (coalesced), and each thread then sums its own face from shared memory in ascending point order
 // (gather_face, the same arithmetic and order as gather_body).  The copies of slot m + 1 are in
-// flight while slot m is summed (two buffers per warp).
+// flight while slot m is summed (two buffers per warp).  GRAD false (residual only): the first three
+// chunks of each record (the flux) are copied.
 
 #define GATHER_WARPS 2                      // warps per block
 #define GATHER_FACE_DOUBLES (4 * CGKS_GPR)  // room for the records of one face: 448 bytes
@@ -31,7 +33,9 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
+template <bool GRAD>
 __global__ void __launch_bounds__(32 * GATHER_WARPS) k_gather(GatherArgs a) {
+  constexpr int CH = GRAD ? CGKS_GPR / 2 : 3;  // 16-byte chunks copied per record
   extern __shared__ __align__(16) double gsm[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t nc = a.nc;
@@ -53,12 +57,15 @@ __global__ void __launch_bounds__(32 * GATHER_WARPS) k_gather(GatherArgs a) {
       ng = (int)(a.gp_ptr[f + 1] - g0);
     }
   };
-  // the 32 faces of one slot into buffer b: face j's 7 x ng 16-byte chunks by lanes 0 .. 7 ng - 1
+  // the 32 faces of one slot into buffer b: chunk c of record k of face j by lane k CH + c, each to
+  // its offset within the face's records (lanes 0 .. CH ng - 1; CH ng <= 28)
+  const int rk = lane / CH, rc = lane - rk * CH;
+  const int off = CGKS_GPR * rk + 2 * rc;
   auto issue = [&](double* b, int64_t g0, int ng) {
     for (int j = 0; j < 32; ++j) {
       const int64_t gj = __shfl_sync(0xffffffffu, g0, j);
       const int nj = __shfl_sync(0xffffffffu, ng, j);
-      if (lane < (CGKS_GPR / 2) * nj) cp_async16(b + j * GATHER_FACE_DOUBLES + 2 * lane, a.gpr + CGKS_GPR * gj + 2 * lane);
+      if (rk < nj) cp_async16(b + j * GATHER_FACE_DOUBLES + off, a.gpr + CGKS_GPR * gj + off);
     }
     cp_async_commit();
   };
@@ -81,7 +88,7 @@ __global__ void __launch_bounds__(32 * GATHER_WARPS) k_gather(GatherArgs a) {
     }
     cp_async_wait_one();
     __syncwarp();
-    if (ng > 0) gather_face(((m & 1) ? buf1 : buf0) + lane * GATHER_FACE_DOUBLES, ng, sg, c);
+    if (ng > 0) gather_face<GRAD>(((m & 1) ? buf1 : buf0) + lane * GATHER_FACE_DOUBLES, ng, sg, c);
     __syncwarp();  // every lane is done with buffer m & 1 before slot m + 2 is copied into it
     g0 = g1;
     ng = n1;
@@ -124,7 +131,7 @@ cgks_status global_min_dt(cgks_ctx* ctx, double* dt, int64_t n) {
   return CGKS_OK;
 }
 
-cgks_status fine_fluxes(cgks_ctx* ctx, const double* W, const double* G, const double* alpha) {
+cgks_status fine_fluxes(cgks_ctx* ctx, const double* W, const double* G, const double* alpha, bool state) {
   const Fine& F = ctx->F;
   const Phys ph = make_phys(ctx->P);
   ReconArgs ra{F.nc, F.nf, F.ctype, F.cf, F.fL, F.fR, F.ftag, F.cside, F.fnrm, F.Kop, F.ggw, F.lsw, F.aux, F.dtw,
@@ -139,9 +146,13 @@ cgks_status fine_fluxes(cgks_ctx* ctx, const double* W, const double* G, const d
   PointArgs pa{F.ngp, F.nf, F.nc, F.gp_face, F.fL, F.fR, F.ftag, F.gp_x, F.gp_A, F.fshift, F.ctr, ctx->rc,
                ctx->dt, ctx->gpr, ph, ctx->derr};
   {
-    ProfScope ps(ctx, PK_POINTS, (double)F.ngp, F.ngp * (52.0 + 8.0 * CGKS_GPR) + F.nf * 36.0 + F.nc * 432.0);
+    ProfScope ps(ctx, state ? PK_POINTS : PK_POINTS_FLUX, (double)F.ngp,
+                 F.ngp * (52.0 + (state ? 8.0 * CGKS_GPR : 40.0)) + F.nf * 36.0 + F.nc * 432.0);
     const int b = spread_block(F.ngp, 128, ctx->n_sm);
-    k_gks_points<<<grid_for(F.ngp, b), b, 0, ctx->stream>>>(pa);
+    if (state)
+      k_gks_points<true><<<grid_for(F.ngp, b), b, 0, ctx->stream>>>(pa);
+    else
+      k_gks_points<false><<<grid_for(F.ngp, b), b, 0, ctx->stream>>>(pa);
   }
   CK(cudaGetLastError());
   return CGKS_OK;
@@ -153,16 +164,23 @@ cgks_status fine_gather(cgks_ctx* ctx, const double* W_in, double* W_out, double
   GatherArgs ga{F.nc, F.ngp, F.ctype, F.cside, F.cf, F.gp_ptr, ctx->gpr, F.vol,
                 ctx->dt, W_in, W_out, res, G_out, alpha_out, update, ctx->P.gamma, ctx->derr};
   {
+    // the residual alone (no gradient, compression factor or update): only the records' fluxes are read
+    const bool grad = G_out || alpha_out || update;
     const double per_cell = 1 + 8 + (update ? 88 : 0) + (res ? 40 : 0) + (G_out ? 120 : 0) + (alpha_out ? 8 : 0);
-    ProfScope ps(ctx, PK_GATHER, (double)F.gp_sides,
-                 F.nc * per_cell + (F.nf + F.n_int + F.n_per) * 5.0 + F.nf * 4.0 + F.ngp * 8.0 * CGKS_GPR);
+    ProfScope ps(ctx, grad ? PK_GATHER : PK_GATHER_RES, (double)F.gp_sides,
+                 F.nc * per_cell + (F.nf + F.n_int + F.n_per) * 5.0 + F.nf * 4.0 + F.ngp * (grad ? 8.0 * CGKS_GPR : 40.0));
     static bool smem_set = false;  // the kernel's dynamic shared memory exceeds the 48 KiB default
     if (!smem_set) {
-      CK(cudaFuncSetAttribute(k_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, GATHER_SMEM));
+      CK(cudaFuncSetAttribute(k_gather<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, GATHER_SMEM));
+      CK(cudaFuncSetAttribute(k_gather<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, GATHER_SMEM));
       smem_set = true;
     }
     const int64_t per_block = 32 * GATHER_WARPS;
-    k_gather<<<(unsigned)((F.nc + per_block - 1) / per_block), 32 * GATHER_WARPS, GATHER_SMEM, ctx->stream>>>(ga);
+    const unsigned nb = (unsigned)((F.nc + per_block - 1) / per_block);
+    if (grad)
+      k_gather<true><<<nb, 32 * GATHER_WARPS, GATHER_SMEM, ctx->stream>>>(ga);
+    else
+      k_gather<false><<<nb, 32 * GATHER_WARPS, GATHER_SMEM, ctx->stream>>>(ga);
   }
   CK(cudaGetLastError());
   return CGKS_OK;

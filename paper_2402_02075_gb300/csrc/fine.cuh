@@ -447,8 +447,8 @@ HD void papp_au(const MomP<T>& P, const T an[5], const T a1[5], const T a2[5], T
 }
 
 // one side of the interface: micro-slopes of the initial distribution, its contribution to the
-// equilibrium slopes, the time-integrated flux, the state at dt and the time-integrated state
-template <typename T>
+// equilibrium slopes, the time-integrated flux, the state at dt (STATE) and the time-integrated state
+template <typename T, bool STATE = true>
 HD void side_terms(const T D[3][5], const T w[5], const Maxw<T>& g, T m0, T m1, T K, T ck,
                    T gm1, T tau, T q4, T q5, T edt, T dtf, T dWc[3][5],
                    T Facc[5], T Wacc[5], T Iacc[5]) {
@@ -495,11 +495,11 @@ HD void side_terms(const T D[3][5], const T w[5], const Maxw<T>& g, T m0, T m1, 
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
     f[q] = q4 * F0[q] - q5 * Fa[q] - tq4 * FA[q];
-    s[q] = edt * V0[q] - etd * Va[q] - etau * VA[q];
+    if (STATE) s[q] = edt * V0[q] - etd * Va[q] - etau * VA[q];
     i[q] = q4 * V0[q] - q5 * Va[q] - tq4 * VA[q];
   }
   add_from_primed<T>(P, f, 1.0, Facc);
-  add_from_primed<T>(P, s, 1.0, Wacc);
+  if (STATE) add_from_primed<T>(P, s, 1.0, Wacc);
   add_from_primed<T>(P, i, 1.0, Iacc);
 }
 
@@ -551,8 +551,10 @@ HD void point_inputs(int64_t g, const PointArgs& a, PointIn& p) {
 
 // the gas-kinetic flux of one Gauss point (flux x weight / dt and interface state x area, both in
 // the global frame) and its compression factor, from the point's left and right states and
-// gradients; on a boundary face (bnd) the right side is the ghost of the left
-template <typename T>
+// gradients; on a boundary face (bnd) the right side is the ghost of the left.  STATE false: the flux
+// alone (the interface state and the compression factor, which only the Gauss-Green gradient update
+// uses, are left out; Wg is not written and alpha is 1)
+template <typename T, bool STATE = true>
 HD void point_flux(const double nd[3], double iw, bool bnd, int tag, const T WLg[5], const T GLg[15], const T WRi[5],
                    const T GRi[15], T dtf, const Phys& ph, T Fg[5], T Wg[5], T& alpha, DevErr* err, int64_t f) {
   T n[3], t1[3], t2[3];
@@ -613,7 +615,7 @@ HD void point_flux(const double nd[3], double iw, bool bnd, int tag, const T WLg
   const T q5 = (tau * tn + tn * tn) * om - tn * dtf * edt;
   // compression factor of this Gauss point (interior faces only), 1/p = l2 / rho
   alpha = 1.0;
-  if (!bnd && ph.cf) {
+  if (STATE && !bnd && ph.cf) {
     const T icl = rsqrt_hd(ph.gamma * gl.h), icr = rsqrt_hd(ph.gamma * gr.h);
     const T dp = fabs(gl.p - gr.p);
     const T dn = gl.U * icl - gr.U * icr, d1 = gl.V * icl - gr.V * icr, d2 = gl.W * icl - gr.W * icr;
@@ -629,9 +631,9 @@ HD void point_flux(const double nd[3], double iw, bool bnd, int tag, const T WLg
   {
     T D[3][5];
     rotate_gradient<T>(GLg, e, D);
-    side_terms<T>(D, wl, gl, ml0, ml1, K, gl.l2 * gl.l2 * iK3, gm1, tau, q4, q5, edt, dtf, dWc, Facc, Wacc, Iacc);
+    side_terms<T, STATE>(D, wl, gl, ml0, ml1, K, gl.l2 * gl.l2 * iK3, gm1, tau, q4, q5, edt, dtf, dWc, Facc, Wacc, Iacc);
     rotate_gradient<T>(GRg, e, D);
-    side_terms<T>(D, wr, gr, mr0, mr1, K, gr.l2 * gr.l2 * iK3, gm1, tau, q4, q5, edt, dtf, dWc, Facc, Wacc, Iacc);
+    side_terms<T, STATE>(D, wr, gr, mr0, mr1, K, gr.l2 * gr.l2 * iK3, gm1, tau, q4, q5, edt, dtf, dWc, Facc, Wacc, Iacc);
   }
   // equilibrium part: slopes a^c from the kinetic-weighted interface gradients; A^c from
   // <A + a.u> = 0; full-space moments through the Euler-flux Jacobians
@@ -674,7 +676,7 @@ HD void point_flux(const double nd[3], double iw, bool bnd, int tag, const T WLg
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
     Facc[q] += q1 * Fc0[q] + q2 * Fca[q] + q3 * FcA[q];
-    Wacc[q] += om * (wc[q] - dtf * cu[q]);
+    if (STATE) Wacc[q] += om * (wc[q] - dtf * cu[q]);
     Iacc[q] += q1 * wc[q] + (q2 - q3) * cu[q];
   }
   if (ph.viscous && ph.prandtl != 1.0) {
@@ -689,19 +691,26 @@ HD void point_flux(const double nd[3], double iw, bool bnd, int tag, const T WLg
 #pragma unroll
   for (int q = 0; q < 5; ++q) Facc[q] *= sdt;
   rotate_out<T>(Facc, n, t1, t2, Fg);
-  rotate_out<T>(Wacc, n, t1, t2, Wg);
+  if (STATE) rotate_out<T>(Wacc, n, t1, t2, Wg);
 }
 
+// one contiguous record per point, so that the gather reads a face's points as one segment; STATE
+// false (the defect of the V-cycle): the flux alone, in the record's first five entries
+template <bool STATE = true>
 HD void gks_point_body(int64_t g, const PointArgs& a) {
   PointIn p;
   point_inputs(g, a, p);
   double Fg[5], Wg[5], alpha;
-  point_flux<double>(p.n, p.iw, p.R < 0, a.ftag[p.f], p.WL, p.GL, p.WR, p.GR, p.dtf, a.ph, Fg, Wg, alpha, a.err, p.f);
+  point_flux<double, STATE>(p.n, p.iw, p.R < 0, a.ftag[p.f], p.WL, p.GL, p.WR, p.GR, p.dtf, a.ph, Fg, Wg, alpha, a.err,
+                            p.f);
   const int64_t ngp = a.ngp;
-  // one contiguous record per point, so that the gather reads a face's points as one segment
   double2* dst = reinterpret_cast<double2*>(a.gpr + (int64_t)CGKS_GPR * g);
   dst[0] = make_double2(Fg[0], Fg[1]);
   dst[1] = make_double2(Fg[2], Fg[3]);
+  if (!STATE) {
+    a.gpr[(int64_t)CGKS_GPR * g + 4] = Fg[4];
+    return;
+  }
   dst[2] = make_double2(Fg[4], Wg[0]);
   dst[3] = make_double2(Wg[1], Wg[2]);
   dst[4] = make_double2(Wg[3], Wg[4]);
@@ -789,10 +798,16 @@ HD double xor_sign(double x, uint64_t mask) {
 
 // adds the ng consecutive Gauss-point records `rec` of one face, seen from its left cell (right:
 // false) or from its right cell (the flux and the area vector change sign), in ascending point order
+template <bool GRAD = true>
 HD void gather_face(const double* rec, int ng, bool right, GatherAcc& c) {
   const uint64_t m = right ? 0x8000000000000000ull : 0ull;
   for (int k = 0; k < ng; ++k) {
     const double* v = rec + (int64_t)CGKS_GPR * k;
+    if (!GRAD) {  // the residual alone (the defect of the V-cycle)
+#pragma unroll
+      for (int q = 0; q < 5; ++q) c.r[q] -= xor_sign(v[q], m);
+      continue;
+    }
     const double A[3] = {xor_sign(v[10], m), xor_sign(v[11], m), xor_sign(v[12], m)};
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
@@ -842,7 +857,13 @@ HD void gather_body(int64_t i, const GatherArgs& a) {
   for (int m = 0; m < nt; ++m) {
     const int64_t f = a.cf[(int64_t)m * nc + i];
     const int64_t g0 = a.gp_ptr[f];
-    gather_face(a.gpr + (int64_t)CGKS_GPR * g0, (int)(a.gp_ptr[f + 1] - g0), a.cside[(int64_t)m * nc + i] != 0, c);
+    const double* rec = a.gpr + (int64_t)CGKS_GPR * g0;
+    const int ng = (int)(a.gp_ptr[f + 1] - g0);
+    const bool right = a.cside[(int64_t)m * nc + i] != 0;
+    if (a.G_out || a.alpha_out || a.update)
+      gather_face<true>(rec, ng, right, c);
+    else
+      gather_face<false>(rec, ng, right, c);
   }
   gather_store(i, a, c);
 }

@@ -97,6 +97,8 @@ enum ProfKind {
   PK_PROLONG,      // k_prolong / k_prolong_smooth: cells of the finer level
   PK_KFVS_JVP,     // k_kfvs_jvp_faces: faces
   PK_NORM,         // k_norm_partial + k_norm_final: cells
+  PK_POINTS_FLUX,  // k_gks_points<false> (the flux alone, the V-cycle's defect): Gauss points
+  PK_GATHER_RES,   // k_gather<false> (the residual alone): Gauss points seen from cells
   PK_COUNT
 };
 
@@ -217,7 +219,9 @@ cgks_status check_device_error(cgks_ctx* ctx, const char* where);
 
 // fine CGKS residual: reconstruct + Gauss-point fluxes; then either a gather into outputs or an
 // explicit update of (W, G, alpha)
-cgks_status fine_fluxes(cgks_ctx* ctx, const double* W, const double* G, const double* alpha);
+// state false: the Gauss-point fluxes alone (no interface state, area or compression factor in the
+// records), for a residual-only gather
+cgks_status fine_fluxes(cgks_ctx* ctx, const double* W, const double* G, const double* alpha, bool state = true);
 cgks_status fine_gather(cgks_ctx* ctx, const double* W_in, double* W_out, double* res, double* G_out,
                         double* alpha_out, int update);
 cgks_status density_norm(cgks_ctx* ctx, const double* res, const double* vol, int64_t n, double* out_dev);

@@ -93,15 +93,17 @@ extern "C" int host_reconstruct(int64_t nc, int64_t nf, const int8_t* ctype, con
   return err.code;
 }
 
-// the whole fine residual (Res, Gnew, alpha) of the CUDA path on the host, and, when rbar != NULL,
-// the adjoint's transposed product (stored Jacobians and the four transposed-product bodies)
+// the whole fine residual (Res, Gnew, alpha) of the CUDA path on the host; when res_flux != NULL,
+// the residual again by the flux-only point body and the residual-only gather (into fresh records);
+// and, when rbar != NULL, the adjoint's transposed product (stored Jacobians and the four
+// transposed-product bodies)
 extern "C" int host_fine(int64_t nc, int64_t nf, int64_t ngp, const int8_t* ctype, const int32_t* cf,
                          const int8_t* cside, const int32_t* fL, const int32_t* fR, const int32_t* ftag,
                          const int32_t* gp_ptr, const int32_t* gp_face, const double* gp_x, const double* gp_A,
                          const double* vol, const double* ctr, const double* m2, const double* Sn, const double* area,
                          const double* fshift, const double* fctr, const double* fnrm, const double* W, const double* G,
                          const double* alpha, const double* p, int cf_on, double* res, double* Gout, double* aout,
-                         const double* rbar, const double* gbar, double* out, int recompute) {
+                         const double* rbar, const double* gbar, double* out, int recompute, double* res_flux) {
   std::vector<double> Kop(216 * nc), ggw(18 * nc), lsw(18 * nc), aux(8 * nc), dtw(24 * nc);
   DevErr err{};
   ROArgs ro{nc, nf, ctype, cf, cside, fL, fR, vol, ctr, m2, Sn, area, fshift, fctr, fnrm,
@@ -131,6 +133,16 @@ extern "C" int host_fine(int64_t nc, int64_t nf, int64_t ngp, const int8_t* ctyp
   GatherArgs ga{nc, ngp, ctype, cside, cf, gp_ptr, gpra, vol, dt.data(), W,
                 nullptr, res, Gout, aout, 0, ph.gamma, &err};
   for (int64_t i = 0; i < nc; ++i) gather_body(i, ga);
+  if (res_flux) {
+    std::vector<double> gpr2(CGKS_GPR * ngp + 2, 0.0);
+    double* g2 = gpr2.data() + ((reinterpret_cast<uintptr_t>(gpr2.data()) & 15) ? 1 : 0);
+    PointArgs pf = pa;
+    pf.gpr = g2;
+    for (int64_t g = 0; g < ngp; ++g) gks_point_body<false>(g, pf);
+    GatherArgs gf{nc, ngp, ctype, cside, cf, gp_ptr, g2, vol, dt.data(), W,
+                  nullptr, res_flux, nullptr, nullptr, 0, ph.gamma, &err};
+    for (int64_t i = 0; i < nc; ++i) gather_body(i, gf);
+  }
   if (err.code || !rbar) return err.code;
   std::vector<double> Jr(recompute ? 1 : (size_t)CGKS_RJ_ROWS * nc), Jp((size_t)CGKS_PJ_IN * CGKS_PJ_OUT * ngp);
   if (!recompute)
@@ -194,7 +206,7 @@ def host(tmp_path_factory):
     L.host_ghost.argtypes = [C.c_int, C.c_double] + [d_] * 6
     L.host_kfvs_jvp32.argtypes = [C.c_double] + [d_] * 6
     L.host_reconstruct.argtypes = [C.c_int64, C.c_int64] + [d_] * 20
-    L.host_fine.argtypes = [C.c_int64] * 3 + [d_] * 22 + [C.c_int] + [d_] * 6 + [C.c_int]
+    L.host_fine.argtypes = [C.c_int64] * 3 + [d_] * 22 + [C.c_int] + [d_] * 6 + [C.c_int, d_]
     return L
 
 
@@ -429,10 +441,12 @@ def test_fine_residual_on_the_host_matches_the_oracle(orc, host, name, cf_on):
     om, nc, nf, ngp, arrays, keep = _fine_inputs(orc, mesh)
     W, G, rng = _state(mg, nc, prm["mach"], 43)
     alpha = 1.0 - 0.1 * rng.random(nc)
-    res, Gout, aout = np.zeros((5, nc)), np.zeros((15, nc)), np.zeros(nc)
+    res, Gout, aout, res_flux = np.zeros((5, nc)), np.zeros((15, nc)), np.zeros(nc), np.full((5, nc), np.nan)
     code = host.host_fine(nc, nf, ngp, *arrays, _p(W), _p(G), _p(alpha), _p(_phys_vector(prm)), cf_on, _p(res),
-                          _p(Gout), _p(aout), None, None, None, 0)
+                          _p(Gout), _p(aout), None, None, None, 0, _p(res_flux))
     assert code == 0
+    # the V-cycle's defect (flux-only points, residual-only gather) is the same residual, bit for bit
+    assert np.array_equal(res_flux, res)
     os_ = orc.Solver(om, orc.params(n_levels=1, compression_factor=cf_on, **prm))
     os_.set_state(W, G, alpha)
     ro = os_.residual()
@@ -471,7 +485,7 @@ def test_adjoint_product_on_the_host_matches_oracle_differences(orc, host, name)
             out = np.zeros((20, nc))
             res, Gout, aout = np.zeros((5, nc)), np.zeros((15, nc)), np.zeros(nc)
             code = host.host_fine(nc, nf, ngp, *arrays, _p(W), _p(G), _p(ones), _p(_phys_vector(prm)), 0, _p(res),
-                                  _p(Gout), _p(aout), _p(w[:5 * nc]), _p(w[5 * nc:]), _p(out), recompute)
+                                  _p(Gout), _p(aout), _p(w[:5 * nc]), _p(w[5 * nc:]), _p(out), recompute, None)
             assert code == 0
             outs.append(out)
         from parity import assert_normwise
