@@ -40,7 +40,7 @@ UNIT = "Mcell-iters/s"
 # V-cycle at a 3e-5 drop with the compression factor on
 WORKLOAD = dict(nx=96, ny=64, nz=69, outflow=5)
 PARAMS = dict(mach=0.5, reynolds=1e4, prandtl=0.72, gamma=1.4, viscous=1, n_levels=3, cfl_fine=0.5,
-              cfl_coarse=0.5, agglo_seed=0)
+              cfl_coarse=0.9, coarse_steps=2, agglo_seed=0)
 # bounded sample of the same workload for the CPU oracle: 4 of its 64 periodic columns in y, i.e. the
 # same x-z layout and physics (82,944 cells)
 SAMPLE = dict(nx=96, ny=4, nz=69, outflow=5)

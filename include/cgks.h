@@ -47,7 +47,7 @@ typedef struct {
   double prandtl;      /* Prandtl number; the BGK model has Pr = 1, other values correct the heat flux */
   double aoa[2];       /* degrees: angle of attack (x-z plane) and sideslip of the free stream */
   double cfl_fine;     /* CFL number of the fine-level local time step */
-  double cfl_coarse;   /* CFL number of the coarse-level (KFVS) local time step */
+  double cfl_coarse;   /* CFL number of the coarse-level (KFVS) local time step (0.9) */
   double eps_inviscid; /* epsilon in tau_n = eps dt + C |p_l - p_r|/(p_l + p_r) dt (Sec. 2.3, 0.01) */
   double c_press;      /* C of the pressure-jump term of tau_n (Sec. 2.3, 1) */
   double weno_eps;     /* epsilon of the non-linear WENO weights (Sec. 3.4, 1e-5) */
@@ -60,7 +60,7 @@ typedef struct {
   int32_t n_levels;    /* multigrid levels including the fine one (Sec. 4.2 uses 3) */
   int32_t pre;         /* fine pre-smoothing steps per V-cycle (Sec. 4.2: 1) */
   int32_t post;        /* post-smoothing steps per level (Sec. 4.2: 0) */
-  int32_t coarse_steps;     /* forward-Euler KFVS steps per coarse level and cycle (1) */
+  int32_t coarse_steps;     /* forward-Euler KFVS steps per coarse level and cycle (2) */
   int32_t passes_per_level; /* pairwise coarsening passes per multigrid level (2) */
   int32_t viscous;     /* 0 Euler, 1 Navier-Stokes (tau = mu/p) */
   int32_t dt_mode;     /* 0 local time steps, 1 one global (minimum) time step per level */

@@ -49,10 +49,11 @@ class Params(C.Structure):
 
 def params(**kw) -> Params:
     """Defaults are the readings of the paper's free constants (eps = 0.01, C = 1, WENO eps = 1e-5,
-    3 levels, 1 pre- and 0 post-smoothing steps, 1 coarse step, 2 passes per level)."""
+    3 levels, 1 pre- and 0 post-smoothing steps, 2 coarse forward-Euler steps at CFL 0.9, 2 passes per
+    level)."""
     d = dict(gamma=1.4, mach=0.2, reynolds=1e4, prandtl=1.0, aoa=(0.0, 0.0), cfl_fine=0.5,
-             cfl_coarse=0.5, eps_inviscid=0.01, c_press=1.0, weno_eps=1e-5, skew_min=0.2, sutherland=0.0, correction_relax=1.0,
-             n_levels=3, pre=1, post=0, coarse_steps=1, passes_per_level=2, viscous=0,
+             cfl_coarse=0.9, eps_inviscid=0.01, c_press=1.0, weno_eps=1e-5, skew_min=0.2, sutherland=0.0, correction_relax=1.0,
+             n_levels=3, pre=1, post=0, coarse_steps=2, passes_per_level=2, viscous=0,
              dt_mode=0, precision=0, coarse_smoother=0, compression_factor=1, prolongation=0, agglo_seed=0)
     d.update(kw)
     p = Params()

@@ -236,7 +236,7 @@ cgks_status cgks_default_params(cgks_params* p) {
   p->reynolds = 1e4;
   p->prandtl = 1.0;
   p->cfl_fine = 0.5;
-  p->cfl_coarse = 0.5;
+  p->cfl_coarse = 0.9;
   p->eps_inviscid = 0.01;
   p->c_press = 1.0;
   p->weno_eps = 1e-5;
@@ -246,7 +246,7 @@ cgks_status cgks_default_params(cgks_params* p) {
   p->n_levels = 3;
   p->pre = 1;
   p->post = 0;
-  p->coarse_steps = 1;
+  p->coarse_steps = 2;
   p->passes_per_level = 2;
   return CGKS_OK;
 }

@@ -9,7 +9,7 @@ so their single-grid state serves every iteration; the boundary layer's nonlinea
 more than one near the leading-edge corner, so it is stored for both iterations and each is compared
 with the same iteration of the library.
 
-  python tests/golden/make_steady_states.py [name ...]
+  python tests/golden/make_steady_states.py [name[:sg|:vc] ...]
 """
 import os
 import sys
@@ -55,13 +55,15 @@ def reference(name, it):
     return path(name, it if it in its else its[0])
 
 
-def make(name, chunk=200):
+def make(name, only=None, chunk=200):
     import oracle
     oracle.build()
     mk, phys, iterations, drop, limit = CASES[name]
     mesh = mk()
     M = oracle.Mesh(mesh)
     for itn in iterations:
+        if only and itn != only:
+            continue
         multigrid = itn == "vc"
         S = oracle.Solver(M, oracle.params(**case_params(name)))
         W, G = mg.uniform_state(M.nc, mach=phys["mach"])
@@ -81,5 +83,7 @@ def make(name, chunk=200):
 
 
 if __name__ == "__main__":
-    for n in sys.argv[1:] or list(CASES):
-        make(n)
+    # arguments: case names, each optionally with ":sg" or ":vc" for one of its iterations
+    for arg in sys.argv[1:] or list(CASES):
+        n, _, it = arg.partition(":")
+        make(n, it or None)

@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 PRM = dict(mach=0.5, reynolds=1e4, prandtl=0.72, gamma=1.4, viscous=1, n_levels=3, cfl_fine=0.5,
-           cfl_coarse=0.5, agglo_seed=0)
+           cfl_coarse=0.9, coarse_steps=2, agglo_seed=0)
 
 
 @pytest.fixture(scope="module")
