@@ -181,9 +181,12 @@ HD void vjp_recon_body(int64_t i, const ReconArgs& a, const VjpArgs& v, const do
         for (int e = 0; e < 3; ++e) Gn[m][e] = gval[m][5 + 3 * q + e];
       }
       const double dQ = Qn[m] - Q0[q];
-      for (int j = 0; j < 9; ++j)
-        b[j] += a.Kop[(j * 24 + m) * nc + i] * dQ + a.Kop[(j * 24 + 6 + 3 * m) * nc + i] * Gn[m][0] +
-                a.Kop[(j * 24 + 7 + 3 * m) * nc + i] * Gn[m][1] + a.Kop[(j * 24 + 8 + 3 * m) * nc + i] * Gn[m][2];
+      for (int j = 0; j < 9; ++j) {  // in the forward reconstruction's order
+        b[j] += a.Kop[(j * 24 + m) * nc + i] * dQ;
+        b[j] += a.Kop[(j * 24 + 6 + 3 * m) * nc + i] * Gn[m][0];
+        b[j] += a.Kop[(j * 24 + 7 + 3 * m) * nc + i] * Gn[m][1];
+        b[j] += a.Kop[(j * 24 + 8 + 3 * m) * nc + i] * Gn[m][2];
+      }
       for (int d = 0; d < 3; ++d) {
         gg[d] += a.ggw[(3 * m + d) * nc + i] * (Qn[m] + Q0[q]);
         gl[d] += a.lsw[(3 * m + d) * nc + i] * dQ;

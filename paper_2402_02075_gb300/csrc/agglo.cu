@@ -420,6 +420,18 @@ static cgks_status coarsen_pass(cgks_ctx* ctx, const Level& P, Level& Q, int32_t
   return CGKS_OK;
 }
 
+// unit normal and length of each face's (summed) area vector, once per level for the KFVS face flux
+// and the coarse time step
+__global__ void k_face_normals(int64_t nf, const double* __restrict__ Sn, double* __restrict__ nS) {
+  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= nf) return;
+  const double S[3] = {Sn[f], Sn[nf + f], Sn[2 * nf + f]};
+  const double s = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) nS[d * nf + f] = s > 0.0 ? S[d] / s : 0.0;
+  nS[3 * nf + f] = s;
+}
+
 cgks_status build_levels(cgks_ctx* ctx) {
   auto& M = ctx->mesh_allocs;
   cudaStream_t st = ctx->stream;
@@ -456,6 +468,10 @@ cgks_status build_levels(cgks_ctx* ctx) {
     CK(cudaStreamSynchronize(st));
     free_list(tmp);
     ctx->L.push_back(cur);
+  }
+  for (Level& L : ctx->L) {
+    CKS(dalloc(ctx, M, &L.nS, 4 * L.nf));
+    k_face_normals<<<grid_for(L.nf, 256), 256, 0, st>>>(L.nf, L.Sn, L.nS);
   }
   ctx->C.assign(ctx->L.size(), CoarseBuf());
   for (size_t l = 1; l < ctx->L.size(); ++l) {

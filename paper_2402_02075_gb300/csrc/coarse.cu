@@ -7,18 +7,17 @@
 
 // KFVS face fluxes x area (FP64)
 __global__ void k_kfvs_faces(int64_t nf, const int32_t* __restrict__ fL, const int32_t* __restrict__ fR,
-                             const int32_t* __restrict__ ftag, const double* __restrict__ Sn, int64_t nc,
+                             const int32_t* __restrict__ ftag, const double* __restrict__ nS, int64_t nc,
                              const double* __restrict__ W, double* __restrict__ ff, Phys ph, DevErr* err) {
   const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (f >= nf) return;
-  const double S[3] = {Sn[f], Sn[nf + f], Sn[2 * nf + f]};
-  const double s = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+  const double s = nS[3 * nf + f];
   if (s == 0.0) {  // a coarse face whose summed area vectors cancel carries no flux
 #pragma unroll
     for (int q = 0; q < 5; ++q) ff[q * nf + f] = 0.0;
     return;
   }
-  const double n[3] = {S[0] / s, S[1] / s, S[2] / s};
+  const double n[3] = {nS[f], nS[nf + f], nS[2 * nf + f]};
   const int64_t L = fL[f], R = fR[f];
   double WL[5], WR[5], F[5];
 #pragma unroll
@@ -94,10 +93,10 @@ __global__ void k_kfvs_gather(int64_t nc, int64_t nf, const int32_t* __restrict_
 }
 
 // local time step CFL |Omega| / sum_p A_p (|u . n_p| + c): A_p the area of the coarse face (the sum
-// of its fine faces' areas), n_p the direction of its summed area vector (no |u . n| term when that
-// vector cancels)
+// of its fine faces' areas), n_p the direction of its summed area vector (nS; zero, so no |u . n|
+// term, when that vector cancels)
 __global__ void k_coarse_dt(int64_t nc, int64_t nf, const int32_t* __restrict__ ptr, const int32_t* __restrict__ c2f,
-                            const double* __restrict__ Sn, const double* __restrict__ area,
+                            const double* __restrict__ nS, const double* __restrict__ area,
                             const double* __restrict__ vol, const double* __restrict__ W,
                             double* __restrict__ dt, double gamma, double cfl) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -109,9 +108,7 @@ __global__ void k_coarse_dt(int64_t nc, int64_t nf, const int32_t* __restrict__ 
   double s = 0.0;
   for (int32_t k = ptr[c]; k < ptr[c + 1]; ++k) {
     const int64_t f = c2f[k];
-    const double S[3] = {Sn[f], Sn[nf + f], Sn[2 * nf + f]};
-    const double a = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
-    const double un = a > 0.0 ? fabs(u[0] * S[0] + u[1] * S[1] + u[2] * S[2]) / a : 0.0;
+    const double un = fabs(u[0] * nS[f] + u[1] * nS[nf + f] + u[2] * nS[2 * nf + f]);
     s += area[f] * (un + snd);
   }
   dt[c] = cfl * vol[c] / s;
@@ -289,9 +286,9 @@ cgks_status kfvs_residual(cgks_ctx* ctx, int lev, const double* W, double* res) 
   double* ff = lev == 0 ? ctx->ffl : ctx->C[lev].ff;
   const double entries = (double)(L.nf + L.n_int + L.n_per);
   {
-    ProfScope ps(ctx, PK_KFVS_FACES, (double)L.nf, L.nf * 76.0 + L.nc * 40.0);
+    ProfScope ps(ctx, PK_KFVS_FACES, (double)L.nf, L.nf * 84.0 + L.nc * 40.0);
     const int b = spread_block(L.nf, 256, ctx->n_sm);
-    k_kfvs_faces<<<grid_for(L.nf, b), b, 0, ctx->stream>>>(L.nf, L.fL, L.fR, L.ftag, L.Sn, L.nc, W, ff, ph, ctx->derr);
+    k_kfvs_faces<<<grid_for(L.nf, b), b, 0, ctx->stream>>>(L.nf, L.fL, L.fR, L.ftag, L.nS, L.nc, W, ff, ph, ctx->derr);
   }
   {
     ProfScope ps(ctx, PK_KFVS_GATHER, (double)L.nc, L.nc * 44.0 + entries * 4.0 + L.nf * 48.0);
@@ -326,7 +323,7 @@ cgks_status coarse_dt(cgks_ctx* ctx, int lev, const double* W, double* dt) {
   {
     ProfScope ps(ctx, PK_COARSE_DT, (double)L.nc, L.nc * 60.0 + (L.nf + L.n_int + L.n_per) * 4.0 + L.nf * 32.0);
     const int b = spread_block(L.nc, 256, ctx->n_sm);
-    k_coarse_dt<<<grid_for(L.nc, b), b, 0, ctx->stream>>>(L.nc, L.nf, L.c2f_ptr, L.c2f, L.Sn, L.area, L.vol, W, dt,
+    k_coarse_dt<<<grid_for(L.nc, b), b, 0, ctx->stream>>>(L.nc, L.nf, L.c2f_ptr, L.c2f, L.nS, L.area, L.vol, W, dt,
                                                           ctx->P.gamma, ctx->P.cfl_coarse);
   }
   if (ctx->P.dt_mode == 1) CKS(global_min_dt(ctx, dt, L.nc));

@@ -113,7 +113,8 @@ HD void reconstruct_cell(int64_t i, const ReconArgs& a, int seed, T out[CGKS_RC]
     T dQ[5];
 #pragma unroll
     for (int q = 0; q < 5; ++q) dQ[q] = Qn[q] - Q0[q];
-    // the difference column and the three gradient columns of this neighbour
+    // the difference column and the three gradient columns of this neighbour, each added into the
+    // coefficient on its own (one fused multiply-add per operator entry)
 #pragma unroll
     for (int j = 0; j < 9; ++j) {
       const double k0 = a.Kop[(j * 24 + m) * nc + i];
@@ -121,7 +122,12 @@ HD void reconstruct_cell(int64_t i, const ReconArgs& a, int seed, T out[CGKS_RC]
       const double ky = a.Kop[(j * 24 + 7 + 3 * m) * nc + i];
       const double kz = a.Kop[(j * 24 + 8 + 3 * m) * nc + i];
 #pragma unroll
-      for (int q = 0; q < 5; ++q) b[q][j] += k0 * dQ[q] + kx * Gn[3 * q] + ky * Gn[3 * q + 1] + kz * Gn[3 * q + 2];
+      for (int q = 0; q < 5; ++q) {
+        b[q][j] += k0 * dQ[q];
+        b[q][j] += kx * Gn[3 * q];
+        b[q][j] += ky * Gn[3 * q + 1];
+        b[q][j] += kz * Gn[3 * q + 2];
+      }
     }
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -394,14 +400,27 @@ HD void to_primed(const MomP<T>& P, const T s[5], T sp[5]) {
   sp[4] = s[4];
 }
 
-// out += c T o'
+// out += T o' (the energy row added term by term, one fused multiply-add each)
 template <typename T>
-HD void add_from_primed(const MomP<T>& P, const T o[5], T c, T out[5]) {
-  out[0] += c * o[0];
-  out[1] += c * o[1];
-  out[2] += c * (P.V * o[0] + o[2]);
-  out[3] += c * (P.W * o[0] + o[3]);
-  out[4] += c * (P.E * o[0] + P.V * o[2] + P.W * o[3] + o[4]);
+HD void add_from_primed(const MomP<T>& P, const T o[5], T out[5]) {
+  out[0] += o[0];
+  out[1] += o[1];
+  out[2] += P.V * o[0] + o[2];
+  out[3] += P.W * o[0] + o[3];
+  out[4] += P.E * o[0];
+  out[4] += P.V * o[2];
+  out[4] += P.W * o[3];
+  out[4] += o[4];
+}
+
+// out = T o'
+template <typename T>
+HD void from_primed(const MomP<T>& P, const T o[5], T out[5]) {
+  out[0] = o[0];
+  out[1] = o[1];
+  out[2] = P.V * o[0] + o[2];
+  out[3] = P.W * o[0] + o[3];
+  out[4] = P.E * o[0] + P.V * o[2] + P.W * o[3] + o[4];
 }
 
 // o' = <u^k (s' . psi') psi'>
@@ -427,7 +446,9 @@ HD void papp_t_add(const MomP<T>& P, const T s[5], T o[5]) {
   const T S4 = 0.5 * P.h * M[k + 2] + P.hs * M[k];
   o[0] += hM0 * s[J];
   o[1] += hM1 * s[J];
-  o[J] += hM0 * s[0] + hM1 * s[1] + S4 * s[4];
+  o[J] += hM0 * s[0];
+  o[J] += hM1 * s[1];
+  o[J] += S4 * s[4];
   o[4] += S4 * s[J];
 }
 
@@ -478,7 +499,7 @@ HD void side_terms(const T D[3][5], const T w[5], const Maxw<T>& g, T m0, T m1, 
   for (int k = 0; k < 3; ++k) {
     T t[5];
     papp<T, 0>(P, a[k], t);
-    add_from_primed<T>(P, t, 1.0, dWc[k]);
+    add_from_primed<T>(P, t, dWc[k]);
   }
   // <(a.u) psi>, <u (a.u) psi>, <A psi>, <u A psi>, <psi>, <u psi>
   T Va[5], Fa[5], VA[5], FA[5];
@@ -498,9 +519,9 @@ HD void side_terms(const T D[3][5], const T w[5], const Maxw<T>& g, T m0, T m1, 
     if (STATE) s[q] = edt * V0[q] - etd * Va[q] - etau * VA[q];
     i[q] = q4 * V0[q] - q5 * Va[q] - tq4 * VA[q];
   }
-  add_from_primed<T>(P, f, 1.0, Facc);
-  if (STATE) add_from_primed<T>(P, s, 1.0, Wacc);
-  add_from_primed<T>(P, i, 1.0, Iacc);
+  add_from_primed<T>(P, f, Facc);
+  if (STATE) add_from_primed<T>(P, s, Wacc);
+  add_from_primed<T>(P, i, Iacc);
 }
 
 struct PointArgs {
@@ -669,15 +690,17 @@ HD void point_flux(const double nd[3], double iw, bool bnd, int tag, const T WLg
     to_primed<T>(P, ac[1], a1);
     to_primed<T>(P, ac[2], a2);
     papp_au<T, 1>(P, a0, a1, a2, o);
-#pragma unroll
-    for (int q = 0; q < 5; ++q) Fca[q] = 0.0;
-    add_from_primed<T>(P, o, 1.0, Fca);
+    from_primed<T>(P, o, Fca);
   }
+  const T q23 = q2 - q3;
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
-    Facc[q] += q1 * Fc0[q] + q2 * Fca[q] + q3 * FcA[q];
+    Facc[q] += q1 * Fc0[q];
+    Facc[q] += q2 * Fca[q];
+    Facc[q] += q3 * FcA[q];
     if (STATE) Wacc[q] += om * (wc[q] - dtf * cu[q]);
-    Iacc[q] += q1 * wc[q] + (q2 - q3) * cu[q];
+    Iacc[q] += q1 * wc[q];
+    Iacc[q] += q23 * cu[q];
   }
   if (ph.viscous && ph.prandtl != 1.0) {
     // heat flux about U^c of the time-integrated distribution, scaled by (1/Pr - 1)

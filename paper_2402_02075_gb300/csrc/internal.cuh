@@ -47,6 +47,7 @@ struct Level {
   double *vol = nullptr, *ctr = nullptr;                          // [nc], [3][nc]
   int32_t *fL = nullptr, *fR = nullptr, *ftag = nullptr, *ftagR = nullptr;  // [nf]
   double *Sn = nullptr, *area = nullptr, *amom = nullptr, *shift = nullptr;  // [3][nf],[nf],[3][nf],[3][nf]
+  double* nS = nullptr;  // [4][nf] unit normal S/|S| (0 where the summed area vectors cancel), |S|
   int32_t *c2f_ptr = nullptr, *c2f = nullptr;                    // cell -> faces, ascending ids
   int32_t *f2c = nullptr;                                        // finer cell -> this level's cell
   int64_t nc_finer = 0;
