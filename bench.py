@@ -47,20 +47,20 @@ SAMPLE = dict(nx=96, ny=4, nz=69, outflow=5)
 # FP64 floating-point operations per Gauss point of the gas-kinetic flux kernel (2 per DFMA, 1 per
 # DADD/DMUL), from the ncu instruction counts of a full capture of the kernel on the 48x32x32 box;
 # the kernel's own arithmetic, all of which the method needs
-FLOP_PER_GP = 3407.3
+FLOP_PER_GP = 3406.5
 # DRAM bytes (read + write) per Gauss point of the same kernel from the same capture (None when the
 # kernel has changed since)
-DRAM_BYTES_PER_GP = 173.7
+DRAM_BYTES_PER_GP = 172.3
 # FP64 operations per unit of the other kernels bound by the FP64 pipe, from ncu instruction counts
 # on the same box (2 per DFMA, 1 per DMUL or DADD; averages over the launches of a V-cycle):
-# reconstruction per cell (DFMA 1,243.4, DMUL 543.6, DADD 355.6), gather with the gradient update per
+# reconstruction per cell (DFMA 1,464.3, DMUL 318.1, DADD 155.6), gather with the gradient update per
 # Gauss point seen from a cell (DFMA 16.06, DMUL 2.17, DADD 5.11), the flux alone of the V-cycle's
-# defect per Gauss point (DFMA 1,192.0, DMUL 623.5, DADD 250.0), coarse KFVS face flux per face (DFMA
+# defect per Gauss point (DFMA 1,220.1, DMUL 593.4, DADD 215.0), coarse KFVS face flux per face (DFMA
 # 290.8, DMUL 89.2, DADD 21.8).  The residual-only gather of the defect (5.6 FLOP per point seen), the
 # coarse time step and the KFVS gather are latency-bound gathers, reported against HBM.
-FLOP_PER_CELL_RECON = 3385.9
+FLOP_PER_CELL_RECON = 3402.2
 FLOP_PER_GP_SIDE_GATHER = 39.39
-FLOP_PER_GP_FLUX = 3257.5
+FLOP_PER_GP_FLUX = 3248.6
 FLOP_PER_FACE_KFVS = 692.6
 ALU_KERNELS = {"k_gks_points": FLOP_PER_GP, "k_reconstruct": FLOP_PER_CELL_RECON,
                "k_gather": FLOP_PER_GP_SIDE_GATHER, "k_kfvs_faces": FLOP_PER_FACE_KFVS,

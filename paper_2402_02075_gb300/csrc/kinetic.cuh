@@ -6,10 +6,6 @@
 
 #include "internal.cuh"
 
-template <typename T>
-struct Prim {
-  T rho, U, V, W, lam;  // density, velocity in the face frame, lambda = rho / (2 p)
-};
 
 template <typename T>
 HD T tsqrt(T x);
@@ -30,6 +26,24 @@ HD double terfc<double>(double x) { return erfc(x); }
 template <>
 HD float terfc<float>(float x) { return erfcf(x); }
 // x^y for an exponent y that is a constant of the model (gamma, 1/(gamma - 1))
+template <typename T>
+HD T trsqrt(T x);
+template <>
+HD double trsqrt<double>(double x) {
+#ifdef __CUDA_ARCH__
+  return rsqrt(x);
+#else
+  return 1.0 / sqrt(x);
+#endif
+}
+template <>
+HD float trsqrt<float>(float x) {
+#ifdef __CUDA_ARCH__
+  return rsqrtf(x);
+#else
+  return 1.0f / sqrtf(x);
+#endif
+}
 template <typename T>
 HD T tpow(T x, T y);
 template <>
@@ -85,6 +99,11 @@ HD Dual<float> texp<Dual<float>>(Dual<float> x) {
 template <>
 HD Dual<float> terfc<Dual<float>>(Dual<float> x) {  // erfc'(x) = -2/sqrt(pi) exp(-x^2)
   return {erfcf(x.v), -1.1283791670955126f * expf(-x.v * x.v) * x.d};
+}
+template <>
+HD Dual<float> trsqrt<Dual<float>>(Dual<float> x) {
+  const float r = trsqrt<float>(x.v);
+  return {r, -0.5f * r * r * r * x.d};
 }
 template <>
 HD Dual<float> tpow<Dual<float>>(Dual<float> x, Dual<float> y) {  // y constant
@@ -146,6 +165,11 @@ template <>
 HD DualD terfc<DualD>(DualD x) { return erfc(x); }
 template <>
 HD DualD tpow<DualD>(DualD x, DualD y) { return pow(x, y.v); }  // y constant
+template <>
+HD DualD trsqrt<DualD>(DualD x) {
+  const double r = trsqrt<double>(x.v);
+  return {r, -0.5 * r * r * r * x.d};
+}
 
 // branchless orthonormal basis (t1, t2) completing the unit normal n (Duff et al., JCGT 6(1), 2017)
 template <typename T>
@@ -162,17 +186,6 @@ HD void face_frame(const T n[3], T t1[3], T t2[3]) {
 }
 
 // conservative state in the face frame -> primitive; false when rho <= 0 or p <= 0
-template <typename T>
-HD bool prim_local(const T w[5], T gm1, Prim<T>& g) {
-  const T r = T(1) / w[0];
-  g.rho = w[0];
-  g.U = w[1] * r;
-  g.V = w[2] * r;
-  g.W = w[3] * r;
-  const T p = gm1 * (w[4] - T(0.5) * (w[1] * g.U + w[2] * g.V + w[3] * g.W));
-  g.lam = T(0.5) * w[0] / p;
-  return w[0] > T(0) && p > T(0);
-}
 
 template <typename T>
 HD void rotate_in(const T W[5], const T n[3], const T t1[3], const T t2[3], T w[5]) {
@@ -192,43 +205,6 @@ HD void rotate_out(const T f[5], const T n[3], const T t1[3], const T t2[3], T F
   F[4] = f[4];
 }
 
-// u-moments <u^0..u^N> over u > 0 (side = +1), u < 0 (side = -1) or all u (side = 0),
-// normalised by rho: <u^(n+2)> = U <u^(n+1)> + (n+1)/(2 lam) <u^n>
-template <typename T, int N>
-HD void u_moments(T U, T lam, int side, T m[N + 1]) {
-  if (side == 0) {
-    m[0] = T(1);
-    m[1] = U;
-  } else {
-    const T sl = tsqrt(lam);
-    const T s = T(side);
-    m[0] = T(0.5) * terfc(-s * sl * U);
-    m[1] = U * m[0] + s * T(0.5) * texp(-lam * U * U) / (sl * T(1.7724538509055160273));
-  }
-  const T h = T(0.5) / lam;
-#pragma unroll
-  for (int n = 0; n + 2 <= N; ++n) m[n + 2] = U * m[n + 1] + T(n + 1) * h * m[n];
-}
-
-// KFVS flux through the face in the local frame: int_{u>0} u psi g^l + int_{u<0} u psi g^r
-template <typename T>
-HD void kfvs_local(const Prim<T>& gl, const Prim<T>& gr, T K, T f[5]) {
-  const Prim<T>* gs[2] = {&gl, &gr};
-#pragma unroll
-  for (int s = 0; s < 2; ++s) {
-    const Prim<T>& g = *gs[s];
-    T m[4];
-    u_moments<T, 3>(g.U, g.lam, s == 0 ? 1 : -1, m);
-    const T h = T(0.5) / g.lam;
-    const T q = g.V * g.V + g.W * g.W + (T(2) + K) * h;  // <v^2> + <w^2> + <xi^2>
-    const T r = g.rho;
-    f[0] = (s ? f[0] : T(0)) + r * m[1];
-    f[1] = (s ? f[1] : T(0)) + r * m[2];
-    f[2] = (s ? f[2] : T(0)) + r * g.V * m[1];
-    f[3] = (s ? f[3] : T(0)) + r * g.W * m[1];
-    f[4] = (s ? f[4] : T(0)) + T(0.5) * r * (m[3] + m[1] * q);
-  }
-}
 
 // ghost state (and gradient when G != nullptr) of a boundary face with outward unit normal n.
 // tag 1 slip wall (mirror), 2 no-slip adiabatic wall (mirror, velocity reversed), 3 farfield by 1D
@@ -341,16 +317,43 @@ HD bool bc_ghost(int tag, const T n[3], const T W[5], const T* G, T Wg[5], T* Gg
   return false;
 }
 
-// KFVS flux in the global frame through a face with unit normal n
+// one side's half of the KFVS flux, int_{s u_n > 0} u_n psi g (s = +1 for the left state, -1 for the
+// right), added into F in the global frame.  With U = u . n, h = p / rho = 1/(2 lambda) and the
+// half-space moments m_k = <u_n^k> / rho: mass rho m1; momentum rho (m1 u + (m2 - U m1) n), since the
+// tangential velocity is carried with the normal flux; energy rho (m3 + m1 (|u|^2 - U^2 + (K+2) h))/2.
+// One division (1/rho) and one reciprocal square root (sqrt(lambda) = 1/sqrt(2 h)) per side.
+template <typename T>
+HD bool kfvs_side(const T w[5], const T n[3], T K, T gm1, T s, T F[5]) {
+  const T r = T(1) / w[0];
+  const T u[3] = {w[1] * r, w[2] * r, w[3] * r};
+  const T u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const T p = gm1 * (w[4] - T(0.5) * (w[1] * u[0] + w[2] * u[1] + w[3] * u[2]));
+  const T h = p * r;
+  const T sl = trsqrt(T(2) * h);  // sqrt(lambda)
+  const T U = u[0] * n[0] + u[1] * n[1] + u[2] * n[2];
+  const T x = sl * U;
+  T m[4];
+  m[0] = T(0.5) * terfc(-s * x);
+  // U m0 + s exp(-lambda U^2) / (2 sqrt(pi lambda)), 1/sqrt(lambda) = 2 h sqrt(lambda)
+  m[1] = U * m[0] + s * T(0.56418958354775628695) * texp(-x * x) * (h * sl);
+  m[2] = U * m[1] + h * m[0];
+  m[3] = U * m[2] + T(2) * h * m[1];
+  const T rho = w[0];
+  const T rm1 = rho * m[1], rn = rho * (m[2] - U * m[1]);
+  F[0] += rm1;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) F[1 + d] += rm1 * u[d] + rn * n[d];
+  F[4] += T(0.5) * rho * (m[3] + m[1] * (u2 - U * U + (T(2) + K) * h));
+  return w[0] > T(0) && p > T(0);
+}
+
+// KFVS flux (int_{u_n > 0} u_n psi g^l + int_{u_n < 0} u_n psi g^r) in the global frame through a
+// face with unit normal n
 template <typename T>
 HD bool kfvs_flux(const T WL[5], const T WR[5], const T n[3], T K, T gm1, T F[5]) {
-  T t1[3], t2[3], wl[5], wr[5], f[5];
-  face_frame(n, t1, t2);
-  rotate_in(WL, n, t1, t2, wl);
-  rotate_in(WR, n, t1, t2, wr);
-  Prim<T> gl, gr;
-  const bool ok = prim_local(wl, gm1, gl) & prim_local(wr, gm1, gr);
-  kfvs_local(gl, gr, K, f);
-  rotate_out(f, n, t1, t2, F);
-  return ok;
+#pragma unroll
+  for (int q = 0; q < 5; ++q) F[q] = T(0);
+  const bool okl = kfvs_side<T>(WL, n, K, gm1, T(1), F);
+  const bool okr = kfvs_side<T>(WR, n, K, gm1, T(-1), F);
+  return okl && okr;
 }
