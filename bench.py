@@ -47,7 +47,7 @@ SAMPLE = dict(nx=96, ny=4, nz=69, outflow=5)
 # FP64 floating-point operations per Gauss point of the gas-kinetic flux kernel (2 per DFMA, 1 per
 # DADD/DMUL), from the ncu instruction counts of a full capture of the kernel on the 48x32x32 box;
 # the kernel's own arithmetic, all of which the method needs
-FLOP_PER_GP = 3406.5
+FLOP_PER_GP = 3249.5
 # DRAM bytes (read + write) per Gauss point of the same kernel from the same capture (None when the
 # kernel has changed since)
 DRAM_BYTES_PER_GP = 172.3
@@ -55,12 +55,12 @@ DRAM_BYTES_PER_GP = 172.3
 # on the same box (2 per DFMA, 1 per DMUL or DADD; averages over the launches of a V-cycle):
 # reconstruction per cell (DFMA 1,464.3, DMUL 318.1, DADD 155.6), gather with the gradient update per
 # Gauss point seen from a cell (DFMA 16.06, DMUL 2.17, DADD 5.11), the flux alone of the V-cycle's
-# defect per Gauss point (DFMA 1,220.1, DMUL 593.4, DADD 215.0), coarse KFVS face flux per face (DFMA
+# defect per Gauss point (DFMA 1,179.1, DMUL 490.4, DADD 230.0), coarse KFVS face flux per face (DFMA
 # 183.8, DMUL 66.5, DADD 30.9: the launches of a V-cycle weighted by their faces).  The residual-only gather of the defect (5.6 FLOP per point seen), the
 # coarse time step and the KFVS gather are latency-bound gathers, reported against HBM.
 FLOP_PER_CELL_RECON = 3402.2
 FLOP_PER_GP_SIDE_GATHER = 39.39
-FLOP_PER_GP_FLUX = 3248.6
+FLOP_PER_GP_FLUX = 3078.6
 FLOP_PER_FACE_KFVS = 464.8
 ALU_KERNELS = {"k_gks_points": FLOP_PER_GP, "k_reconstruct": FLOP_PER_CELL_RECON,
                "k_gather": FLOP_PER_GP_SIDE_GATHER, "k_kfvs_faces": FLOP_PER_FACE_KFVS,

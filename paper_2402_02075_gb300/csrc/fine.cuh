@@ -255,16 +255,19 @@ HD void recon_jacobian_body(int64_t i, const ReconArgs& a, double* Jr) {
 
 // ---- gas-kinetic point flux -------------------------------------------------------------------
 
-// a Maxwellian in the face frame with the reciprocals the moments and slopes need
+// a Maxwellian in the face frame with the reciprocals and products the moments and slopes need
 template <typename T>
 struct Maxw {
   T rho, U, V, W;  // density, velocity (normal, tangential 1, tangential 2)
   T r, p, h;       // 1/rho, pressure, h = p/rho = 1/(2 lambda)
   T l2, q2;        // 2 lambda = 1/h, |U|^2 + (K+3) h
+  T lr, ckr, hq2;  // 2 lambda / rho, 4 lambda^2 / ((K+3) rho), q2 / 2: the slope solve's coefficients
+  T hu2, rH;       // |U|^2 / 2, (E + p) / rho: the Euler-flux derivative's
 };
 
+// iK3 = 1/(K+3)
 template <typename T>
-HD bool make_maxw(const T w[5], T gm1, T K, Maxw<T>& g) {
+HD bool make_maxw(const T w[5], T gm1, T K, T iK3, Maxw<T>& g) {
   g.rho = w[0];
   g.r = 1.0 / w[0];
   g.U = w[1] * g.r;
@@ -273,7 +276,13 @@ HD bool make_maxw(const T w[5], T gm1, T K, Maxw<T>& g) {
   g.p = gm1 * (w[4] - 0.5 * (w[1] * g.U + w[2] * g.V + w[3] * g.W));
   g.h = g.p * g.r;
   g.l2 = 1.0 / g.h;
-  g.q2 = g.U * g.U + g.V * g.V + g.W * g.W + (K + 3.0) * g.h;
+  const T u2 = g.U * g.U + g.V * g.V + g.W * g.W;
+  g.q2 = u2 + (K + 3.0) * g.h;
+  g.lr = g.l2 * g.r;
+  g.ckr = g.l2 * g.l2 * iK3 * g.r;
+  g.hq2 = 0.5 * g.q2;
+  g.hu2 = 0.5 * u2;
+  g.rH = (w[4] + g.p) * g.r;
   return w[0] > 0.0 && g.p > 0.0;
 }
 
@@ -288,34 +297,35 @@ HD void half_seeds(const Maxw<T>& g, T side, T& m0, T& m1) {
   m1 = g.U * m0 + side * (0.5 * 0.56418958354775628695) * exp(-lam * g.U * g.U) * isl;
 }
 
-// micro-slope s with <s psi> = dW under the full Maxwellian g (closed form of the 5x5 system);
-// ck = 4 lambda^2 / (K + 3)
+// micro-slope s with <s psi> = dW under the full Maxwellian g (closed form of the 5x5 system, with
+// d = dW / rho: s4 = 4 lambda^2/(K+3) (2 d4 - q2 d0 - 2 U.(d - U d0)), s_i = 2 lambda (d_i - U_i d0)
+// - U_i s4, s0 = d0 - U.s - q2 s4 / 2); the 1/rho of d rides in the coefficients lr and ckr
 template <typename T>
-HD void slope_solve(const Maxw<T>& g, T ck, const T dW[5], T s[5]) {
-  const T d0 = dW[0] * g.r, d1 = dW[1] * g.r, d2 = dW[2] * g.r, d3 = dW[3] * g.r, d4 = dW[4] * g.r;
-  const T R4 = 2.0 * d4 - g.q2 * d0;
-  const T R1 = d1 - g.U * d0, R2 = d2 - g.V * d0, R3 = d3 - g.W * d0;
-  s[4] = ck * (R4 - 2.0 * (g.U * R1 + g.V * R2 + g.W * R3));
-  s[1] = g.l2 * R1 - g.U * s[4];
-  s[2] = g.l2 * R2 - g.V * s[4];
-  s[3] = g.l2 * R3 - g.W * s[4];
-  s[0] = d0 - g.U * s[1] - g.V * s[2] - g.W * s[3] - 0.5 * s[4] * g.q2;
+HD void slope_solve(const Maxw<T>& g, const T dW[5], T s[5]) {
+  const T R1 = dW[1] - g.U * dW[0], R2 = dW[2] - g.V * dW[0], R3 = dW[3] - g.W * dW[0];
+  const T R4 = 2.0 * dW[4] - g.q2 * dW[0];
+  s[4] = g.ckr * (R4 - 2.0 * (g.U * R1 + g.V * R2 + g.W * R3));
+  s[1] = g.lr * R1 - g.U * s[4];
+  s[2] = g.lr * R2 - g.V * s[4];
+  s[3] = g.lr * R3 - g.W * s[4];
+  s[0] = g.r * dW[0] - g.U * s[1] - g.V * s[2] - g.W * s[3] - g.hq2 * s[4];
 }
 
 // directional derivative of the Euler flux through the k-th axis of the face frame along dW:
-// equals <u_k (a . psi) psi> under the full Maxwellian when <a psi> = dW
+// equals <u_k (a . psi) psi> under the full Maxwellian when <a psi> = dW.  With e_j = rho du_j =
+// dW_{1+j} - u_j dW_0: d(rho u_k u_j) = dW_{1+k} u_j + u_k e_j, d(u_k (E + p)) = e_k (E + p)/rho +
+// u_k (dE + dp)
 template <typename T>
-HD void euler_jvp(const T w[5], const Maxw<T>& g, T gm1, int k, const T dW[5], T out[5]) {
+HD void euler_jvp(const Maxw<T>& g, T gm1, int k, const T dW[5], T out[5]) {
   const T u[3] = {g.U, g.V, g.W};
-  const T du[3] = {(dW[1] - u[0] * dW[0]) * g.r, (dW[2] - u[1] * dW[0]) * g.r, (dW[3] - u[2] * dW[0]) * g.r};
-  const T dp = gm1 * (dW[4] - (u[0] * dW[1] + u[1] * dW[2] + u[2] * dW[3]) +
-                           0.5 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) * dW[0]);
-  const T mk = w[1 + k], dmk = dW[1 + k];
+  const T e[3] = {dW[1] - u[0] * dW[0], dW[2] - u[1] * dW[0], dW[3] - u[2] * dW[0]};
+  const T dp = gm1 * (dW[4] - (u[0] * dW[1] + u[1] * dW[2] + u[2] * dW[3]) + g.hu2 * dW[0]);
+  const T dmk = dW[1 + k];
   out[0] = dmk;
 #pragma unroll
-  for (int j = 0; j < 3; ++j) out[1 + j] = dmk * u[j] + mk * du[j];
+  for (int j = 0; j < 3; ++j) out[1 + j] = dmk * u[j] + u[k] * e[j];
   out[1 + k] += dp;
-  out[4] = du[k] * (w[4] + g.p) + u[k] * (dW[4] + dp);
+  out[4] = e[k] * g.rH + u[k] * (dW[4] + dp);
 }
 
 // gradient (global frame) of a reconstruction polynomial at offset X from its centroid
@@ -369,18 +379,21 @@ struct MomP {
   T h, sig, tau4;    // h = p/rho, sig = h + <xi^2>/2, tau4 = 2 h^2 + h <xi^2> + <xi^4>/4
   T hs;              // h (2 h + <xi^2>/2)
   T V, W, E;         // tangential velocity and (V^2 + W^2)/2
+  // the matrix entries the products below share, formed once per moment set: P_k = M_{k+2}/2 +
+  // sig M_k (<u^k psi'_0 psi'_4>; <u^k psi'_1 psi'_4> is P_{k+1}), R_k = M_{k+4}/4 + sig M_{k+2} +
+  // tau4 M_k (<u^k psi'_4 psi'_4>), h M_k, and S_k = h M_{k+2}/2 + hs M_k (<u^k c psi'_2 psi'_4>)
+  T Pm[4], Rm[3], hM[4], S4[2];
 };
 
 template <typename T>
 HD void make_momp(const Maxw<T>& g, T m0, T m1, T K, MomP<T>& P) {
-  T m[7];
-  m[0] = m0;
-  m[1] = m1;
+  T* M = P.M;
+  const T h = g.h;
+  M[0] = g.rho * m0;
+  M[1] = g.rho * m1;
 #pragma unroll
-  for (int n = 0; n + 2 < 7; ++n) m[n + 2] = g.U * m[n + 1] + (n + 1) * g.h * m[n];
-#pragma unroll
-  for (int k = 0; k < 7; ++k) P.M[k] = g.rho * m[k];
-  const T h = g.h, x2 = K * h, x4 = K * (K + 2.0) * h * h;
+  for (int n = 0; n + 2 < 7; ++n) M[n + 2] = g.U * M[n + 1] + T(n + 1) * h * M[n];
+  const T x2 = K * h, x4 = K * (K + 2.0) * h * h;
   P.h = h;
   P.sig = h + 0.5 * x2;
   P.tau4 = 2.0 * h * h + h * x2 + 0.25 * x4;
@@ -388,6 +401,15 @@ HD void make_momp(const Maxw<T>& g, T m0, T m1, T K, MomP<T>& P) {
   P.V = g.V;
   P.W = g.W;
   P.E = 0.5 * (g.V * g.V + g.W * g.W);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    P.Pm[k] = 0.5 * M[k + 2] + P.sig * M[k];
+    P.hM[k] = h * M[k];
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) P.Rm[k] = 0.25 * M[k + 4] + P.sig * M[k + 2] + P.tau4 * M[k];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) P.S4[k] = 0.5 * P.hM[k + 2] + P.hs * M[k];
 }
 
 // s' = T^T s
@@ -427,10 +449,7 @@ HD void from_primed(const MomP<T>& P, const T o[5], T out[5]) {
 template <typename T, int k>
 HD void papp(const MomP<T>& P, const T s[5], T o[5]) {
   const T* M = P.M;
-  const T Pk = 0.5 * M[k + 2] + P.sig * M[k];
-  const T Qk = 0.5 * M[k + 3] + P.sig * M[k + 1];
-  const T Rk = 0.25 * M[k + 4] + P.sig * M[k + 2] + P.tau4 * M[k];
-  const T hM = P.h * M[k];
+  const T Pk = P.Pm[k], Qk = P.Pm[k + 1], Rk = P.Rm[k], hM = P.hM[k];
   o[0] = M[k] * s[0] + M[k + 1] * s[1] + Pk * s[4];
   o[1] = M[k + 1] * s[0] + M[k + 2] * s[1] + Qk * s[4];
   o[2] = hM * s[2];
@@ -441,9 +460,7 @@ HD void papp(const MomP<T>& P, const T s[5], T o[5]) {
 // o' += <u^k c (s' . psi') psi'> (J = 2) or <u^k d (s' . psi') psi'> (J = 3)
 template <typename T, int k, int J>
 HD void papp_t_add(const MomP<T>& P, const T s[5], T o[5]) {
-  const T* M = P.M;
-  const T hM0 = P.h * M[k], hM1 = P.h * M[k + 1];
-  const T S4 = 0.5 * P.h * M[k + 2] + P.hs * M[k];
+  const T hM0 = P.hM[k], hM1 = P.hM[k + 1], S4 = P.S4[k];
   o[0] += hM0 * s[J];
   o[1] += hM1 * s[J];
   o[J] += hM0 * s[0];
@@ -470,8 +487,7 @@ HD void papp_au(const MomP<T>& P, const T an[5], const T a1[5], const T a2[5], T
 // one side of the interface: micro-slopes of the initial distribution, its contribution to the
 // equilibrium slopes, the time-integrated flux, the state at dt (STATE) and the time-integrated state
 template <typename T, bool STATE = true>
-HD void side_terms(const T D[3][5], const T w[5], const Maxw<T>& g, T m0, T m1, T K, T ck,
-                   T gm1, T tau, T q4, T q5, T edt, T dtf, T dWc[3][5],
+HD void side_terms(const T D[3][5], const Maxw<T>& g, T m0, T m1, T K, T gm1, T tau, T q4, T q5, T edt, T dtf, T dWc[3][5],
                    T Facc[5], T Wacc[5], T Iacc[5]) {
   MomP<T> P;
   make_momp<T>(g, m0, m1, K, P);
@@ -479,19 +495,19 @@ HD void side_terms(const T D[3][5], const T w[5], const Maxw<T>& g, T m0, T m1, 
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     T s[5];
-    slope_solve<T>(g, ck, D[k], s);
+    slope_solve<T>(g, D[k], s);
     to_primed<T>(P, s, a[k]);
   }
   // time slope A from <A + a.u> = 0 under the full Maxwellian: <(a.u) psi> = sum_k J_k dW_k
   T Ap[5];
   {
     T t0[5], t1[5], t2[5], au[5], A[5];
-    euler_jvp<T>(w, g, gm1, 0, D[0], t0);
-    euler_jvp<T>(w, g, gm1, 1, D[1], t1);
-    euler_jvp<T>(w, g, gm1, 2, D[2], t2);
+    euler_jvp<T>(g, gm1, 0, D[0], t0);
+    euler_jvp<T>(g, gm1, 1, D[1], t1);
+    euler_jvp<T>(g, gm1, 2, D[2], t2);
 #pragma unroll
     for (int q = 0; q < 5; ++q) au[q] = -(t0[q] + t1[q] + t2[q]);
-    slope_solve<T>(g, ck, au, A);
+    slope_solve<T>(g, au, A);
     to_primed<T>(P, A, Ap);
   }
   // half-space moments: equilibrium-slope contributions <a_k psi>
@@ -597,7 +613,7 @@ HD void point_flux(const double nd[3], double iw, bool bnd, int tag, const T WLg
   rotate_in<T>(WLg, n, t1, t2, wl);
   rotate_in<T>(WRg, n, t1, t2, wr);
   Maxw<T> gl, gr;
-  const bool okl = make_maxw<T>(wl, gm1, K, gl), okr = make_maxw<T>(wr, gm1, K, gr);
+  const bool okl = make_maxw<T>(wl, gm1, K, iK3, gl), okr = make_maxw<T>(wr, gm1, K, iK3, gr);
   if (!(okl && okr)) set_err(err, CGKS_ENAN, (int)f, 4);
   // half-space seeds of both sides, and the interface equilibrium
   // W^c = int_{u>0} psi g^l + int_{u<0} psi g^r (Eq. compatibility2)
@@ -616,7 +632,7 @@ HD void point_flux(const double nd[3], double iw, bool bnd, int tag, const T WLg
     wc[4] = 0.5 * (gl.rho * (ml2 + ml0 * ql) + gr.rho * (mr2 + mr0 * qr));
   }
   Maxw<T> gc;
-  if (!make_maxw<T>(wc, gm1, K, gc)) set_err(err, CGKS_ENAN, (int)f, 5);
+  if (!make_maxw<T>(wc, gm1, K, iK3, gc)) set_err(err, CGKS_ENAN, (int)f, 5);
   // collision times (Sec. 2.3)
   const T jump = fabs((gl.p - gr.p) / (gl.p + gr.p));
   T tau, tn;
@@ -652,22 +668,21 @@ HD void point_flux(const double nd[3], double iw, bool bnd, int tag, const T WLg
   {
     T D[3][5];
     rotate_gradient<T>(GLg, e, D);
-    side_terms<T, STATE>(D, wl, gl, ml0, ml1, K, gl.l2 * gl.l2 * iK3, gm1, tau, q4, q5, edt, dtf, dWc, Facc, Wacc, Iacc);
+    side_terms<T, STATE>(D, gl, ml0, ml1, K, gm1, tau, q4, q5, edt, dtf, dWc, Facc, Wacc, Iacc);
     rotate_gradient<T>(GRg, e, D);
-    side_terms<T, STATE>(D, wr, gr, mr0, mr1, K, gr.l2 * gr.l2 * iK3, gm1, tau, q4, q5, edt, dtf, dWc, Facc, Wacc, Iacc);
+    side_terms<T, STATE>(D, gr, mr0, mr1, K, gm1, tau, q4, q5, edt, dtf, dWc, Facc, Wacc, Iacc);
   }
   // equilibrium part: slopes a^c from the kinetic-weighted interface gradients; A^c from
   // <A + a.u> = 0; full-space moments through the Euler-flux Jacobians
-  const T ckc = gc.l2 * gc.l2 * iK3;
   T ac[3][5];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) slope_solve<T>(gc, ckc, dWc[k], ac[k]);
+  for (int k = 0; k < 3; ++k) slope_solve<T>(gc, dWc[k], ac[k]);
   T cu[5];  // <(a^c . u) psi>_c = sum_k J_k dW^c_k
   {
     T u0[5], u1[5], u2[5];
-    euler_jvp<T>(wc, gc, gm1, 0, dWc[0], u0);
-    euler_jvp<T>(wc, gc, gm1, 1, dWc[1], u1);
-    euler_jvp<T>(wc, gc, gm1, 2, dWc[2], u2);
+    euler_jvp<T>(gc, gm1, 0, dWc[0], u0);
+    euler_jvp<T>(gc, gm1, 1, dWc[1], u1);
+    euler_jvp<T>(gc, gm1, 2, dWc[2], u2);
 #pragma unroll
     for (int q = 0; q < 5; ++q) cu[q] = u0[q] + u1[q] + u2[q];
   }
@@ -679,7 +694,7 @@ HD void point_flux(const double nd[3], double iw, bool bnd, int tag, const T WLg
     Fc0[2] = wc[2] * gc.U;
     Fc0[3] = wc[3] * gc.U;
     Fc0[4] = (wc[4] + gc.p) * gc.U;
-    euler_jvp<T>(wc, gc, gm1, 0, cu, FcA);
+    euler_jvp<T>(gc, gm1, 0, cu, FcA);
 #pragma unroll
     for (int q = 0; q < 5; ++q) FcA[q] = -FcA[q];
     // <u (a^c . u) psi>_c in the frame moving with the tangential velocity
