@@ -282,6 +282,33 @@ def test_kfvs_body_matches_the_oracle(orc, host):
         assert np.abs(F - Fo).max() <= 1e-13 * np.abs(Fo).max(), (F, Fo)
 
 
+def _prim_state(rho, u, p, gamma=1.4):
+    u = np.asarray(u, dtype=np.float64)
+    return np.array([rho, *(rho * u), p / (gamma - 1.0) + 0.5 * rho * u @ u])
+
+
+@pytest.mark.parametrize("name,WL,WR,n", [
+    # one-sided fluxes: supersonic along +n and along -n (the half-space erfc tails vanish)
+    ("supersonic +n", _prim_state(1.0, [3.0, 0.2, -0.1], 1 / 1.4), _prim_state(1.2, [2.9, 0.1, 0.0], 0.8), [1.0, 0.0, 0.0]),
+    ("hypersonic -n", _prim_state(0.9, [0.0, 0.0, 8.0], 0.7), _prim_state(1.0, [0.1, 0.0, 8.2], 0.72), [0.0, 0.0, -1.0]),
+    # flow tangential to the face: U = 0, the energy flux carries |u|^2 - U^2 = |u_t|^2
+    ("tangential", _prim_state(1.0, [0.0, 0.9, 0.4], 0.7), _prim_state(1.1, [0.0, 0.8, 0.5], 0.75), [1.0, 0.0, 0.0]),
+    # strong jumps across an oblique face
+    ("strong jump", _prim_state(5.0, [0.3, -0.2, 0.1], 4.0), _prim_state(0.2, [-0.4, 0.3, 0.0], 0.1),
+     [0.48, -0.6, 0.64]),
+])
+def test_kfvs_body_one_sided_tangential_and_jumps(orc, host, name, WL, WR, n):
+    """The coarse KFVS flux in the global frame at the states the random cases do not reach, against
+    the oracle's face-frame KFVS (1e-13 of the flux scale)."""
+    op = orc.params()
+    n = np.asarray(n, dtype=np.float64)
+    n = n / np.linalg.norm(n)
+    F = np.zeros(5)
+    host.host_kfvs(1.4, _p(WL), _p(WR), _p(n), _p(F))
+    Fo = orc.kfvs_point(op, WL, WR, n)
+    assert np.abs(F - Fo).max() <= 1e-13 * np.abs(Fo).max(), (name, F, Fo)
+
+
 @pytest.mark.parametrize("tag", [1, 2, 3, 4, 5])
 def test_ghost_states_match_the_oracle(orc, host, tag):
     """Ghost states and gradients of the five boundary kinds (slip wall, no-slip wall, farfield by
