@@ -1,9 +1,11 @@
-"""Pins of three oracle parts whose only other checks were parity or invariants that a plausible
-mistake would survive:
+"""Pins of oracle parts whose only other checks were parity or invariants that a plausible mistake
+would survive:
 
 - the local time step (a free reading of the paper's local time stepping, Sec. 4.2 and 4.3):
   dt_i = CFL |Omega_i| / sum_p S_p (|U_i . n_p| + c_i + 2 nu_i S_p / |Omega_i|), nu = mu / rho, worked
-  out here from node coordinates of single hand-built cells;
+  out here from node coordinates of single hand-built cells, and on the coarse KFVS levels from the
+  grid lines of a graded Cartesian box and the coarse maps (each coarse face's summed area and the
+  direction of its summed area vector);
 - the skewness confirmation of the coarsening (Sec. 4.1, Eqs. virtual center and skewness factor,
   read as the cosine between d_f = face centre - C_c and the face normal over the faces of the merged
   cell that are not between its two halves, C_c the volume-weighted centre): a hand-built pair whose
@@ -248,3 +250,63 @@ def test_coarsening_volumes_equal_the_solver_volumes(orc, mk):
         agg = np.zeros(L["nc"])
         np.add.at(agg, L["map"], V if lev == 1 else F["vol"])
         assert np.abs(agg - L["vol"]).max() <= 1e-13 * L["vol"].max()
+
+
+def test_coarse_time_step_from_grid_lines(orc):
+    """The KFVS levels' local time step (reading 12 without the viscous term: dt_c = CFL |Omega_c| /
+    sum_p A_p (|u . n_p| + c), A_p the summed area of the fine faces that make coarse face p and n_p
+    the direction of their summed area vector) on a graded Cartesian box, worked out here from the
+    grid lines and the coarse maps alone: a coarse face is the set of fine faces between the same two
+    coarse cells, or of one coarse cell on boundary sides with the same tag (reading 10)."""
+    xs = np.cumsum(np.r_[0.0, 0.10, 0.15, 0.12, 0.20, 0.18, 0.25])
+    ys = np.cumsum(np.r_[0.0, 0.30, 0.20, 0.25, 0.15, 0.10])
+    zs = np.cumsum(np.r_[0.0, 0.05, 0.08, 0.12, 0.30])
+    bc = dict(xmin=4, xmax=5, ymin=1, ymax=1, zmin=2, zmax=3)
+    mesh = mg.box_mesh(6, 5, 4, lambda i, j, k: np.zeros(np.shape(i), dtype=int), xs=xs, ys=ys, zs=zs, bc=bc)
+    M = orc.Mesh(mesh)
+    S = orc.Solver(M, orc.params(n_levels=3, cfl_coarse=0.9, mach=0.5))
+    rho, u, p = 1.1, np.array([0.3, -0.2, 0.1]), 0.9
+    c = np.sqrt(GAMMA * p / rho)
+    # fine cells by grid index, from their node means
+    lines = (xs, ys, zs)
+    dims = (6, 5, 4)
+    idx = {}
+    for cell in range(len(mesh["cell_type"])):
+        m = _cell_nodes(mesh, cell).mean(0)
+        idx[tuple(int(np.searchsorted(lines[a], m[a])) - 1 for a in range(3))] = cell
+    assert len(idx) == 120
+    width = [np.diff(l) for l in lines]
+    side_tag = {(0, -1): 4, (0, 1): 5, (1, -1): 1, (1, 1): 1, (2, -1): 2, (2, 1): 3}
+    cmap = np.arange(120)
+    for lev in (1, 2):
+        L = S.level(lev)
+        cmap = L["map"][cmap]  # fine cell -> cell of this level
+        groups = {}  # (coarse cell, key) -> [summed area vector, summed area]
+        for (i, j, k), a in idx.items():
+            ijk = (i, j, k)
+            for axis in range(3):
+                area = np.prod([width[b][ijk[b]] for b in range(3) if b != axis])
+                for sgn in (-1, 1):
+                    nb = list(ijk)
+                    nb[axis] += sgn
+                    if 0 <= nb[axis] < dims[axis]:
+                        B = cmap[idx[tuple(nb)]]
+                        if B == cmap[a]:
+                            continue
+                        key = ("cell", int(B))
+                    else:
+                        key = ("tag", side_tag[(axis, sgn)])
+                    g = groups.setdefault((int(cmap[a]), key), [np.zeros(3), 0.0])
+                    g[0][axis] += sgn * area
+                    g[1] += area
+        vol = np.zeros(L["nc"])
+        np.add.at(vol, cmap[[idx[t] for t in idx]], [np.prod([width[b][t[b]] for b in range(3)]) for t in idx])
+        denom = np.zeros(L["nc"])
+        for (A, _), (Sv, area) in groups.items():
+            s = np.linalg.norm(Sv)
+            denom[A] += area * ((abs(u @ Sv) / s if s > 0 else 0.0) + c)
+        expected = 0.9 * vol / denom
+        W = np.tile(_state(rho, u, p)[:, None], (1, L["nc"]))
+        got = S.level_dt(lev, W)
+        np.testing.assert_allclose(got, expected, rtol=1e-12, atol=0)
+        assert L["nc"] < 120 and len(groups) > L["nc"]  # cells really merged, faces really grouped
