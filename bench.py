@@ -609,11 +609,13 @@ def run_reference(args):
     value = M.nc * args.steps / dt / 1e6
     cores = int(os.environ.get("OMP_NUM_THREADS", host_cores()))
     sample = (f"each step one V-cycle of the same layout and physics at {SAMPLE['nx']}x{SAMPLE['ny']}x{SAMPLE['nz']} "
-              f"({M.nc:,} cells) instead of the full 96x64x64 box")
+              f"({M.nc:,} cells: {SAMPLE['ny']} of the workload's {WORKLOAD['ny']} periodic columns) instead of the "
+              f"full {WORKLOAD['nx']}x{WORKLOAD['ny']}x{WORKLOAD['nz']} box; the metric is a per-cell rate")
     print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
                       "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                      "data": "synthetic", "config": {"workload": workload_name(SAMPLE)},
+                      "data": "synthetic",
+                      "config": {"workload": workload_name(WORKLOAD), "params": {k: v for k, v in PARAMS.items()}},
                       "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                                        "sample": sample},
                       "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
