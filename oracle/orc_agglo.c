@@ -15,7 +15,8 @@
  *  - skewness: for every face of L or R that is not between them, with d = face centre - C_c and
  *    S n its area vector, sin(alpha) = |d . n| / |d|; the merge is confirmed when
  *    (d . S n)^2 >= skew_min^2 |d|^2 |S n|^2 holds for all of them (IEEE operations in this order,
- *    no FMA);
+ *    no FMA); the measure is pinned by a hand-built pair, the limit skew_min (0.2 by default) is
+ *    not given by the paper (parity unpinned);
  *  - merging is a pairwise matching: confirmed faces in ascending order merge their cells only when
  *    both are still unmatched in this pass;
  *  - coarse cells are numbered in the order of their smallest member; coarse volume V_a + V_b and

@@ -9,13 +9,14 @@
  *
  * Readings (paper silent/garbled):
  *  - gradients of the equilibrium state at the interface are kinetic-weighted, in the same way as
- *    W^c:  dW^c/dx_i = int_{u>0} psi a^l_i g^l + int_{u<0} psi a^r_i g^r;
+ *    W^c:  dW^c/dx_i = int_{u>0} psi a^l_i g^l + int_{u<0} psi a^r_i g^r (parity unpinned: the
+ *    paper prints no number for this choice; its half-space terms are pinned by quadrature);
  *  - inviscid flow: tau := tau_n (Sec. 2.3 numerical collision time) in every term; viscous flow:
  *    tau = mu / p^c in the polynomial terms, tau_n = tau + C |p_l - p_r|/(p_l + p_r) dt in the
  *    exponentials;
  *  - Prandtl number: the BGK model gives Pr = 1 (Eq. ce-ns); for Pr != 1 the time-integrated
  *    energy flux is corrected by (1/Pr - 1) times the time-integrated heat flux about the
- *    interface velocity U^c;
+ *    interface velocity U^c (parity unpinned beyond its smooth-flow Chapman-Enskog form);
  *  - local frame (n, t1, t2) by the branchless orthonormal basis of Duff et al. (JCGT 2017).
  */
 #include <math.h>
